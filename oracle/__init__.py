@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for ALS-WR and ALS-NCG (arXiv 1508.03110).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA path and the CUDA path never imports it.
+
+Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``):
+  loss            pinned: closed-form global minimum of the fully observed case,
+                  U=M=0 value, finite differences of ``grad`` against it
+  grad            pinned: central finite differences of ``loss``
+  half_sweep      pinned: block gradient vanishes after each half (Eq. 3/4
+                  optimality), ridge least squares via numpy lstsq
+  chol_solve      pinned: numpy.linalg.solve on random SPD matrices
+  ls_coeffs       pinned: Q(alpha) equals loss(x + alpha p) at five alphas,
+                  c1 equals grad . p
+  backtracking    pinned: Armijo acceptance/rejection invariants of Algorithm 3
+  ncg (Alg. 2)    pinned: equals textbook preconditioned CG on a convex quadratic
+  als / alsncg    pinned: reach the closed-form global minimum of a fully
+                  observed problem; ALS decreases f monotonically
+  foldin          pinned: equals the user half-sweep row for a user already in R
+"""
+from .core import (  # noqa: F401
+    Problem, build_problem, loss, grad, half_sweep, sweep, ls_coeffs, chol_solve,
+    foldin, q_eval, backtracking, exact_step, ncg, als, alsncg, set_threads,
+    get_threads, IterRecord,
+)

@@ -1,0 +1,8 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the
+benchmark.  This package holds only random-number generation and shaping of
+ratings matrices; none of the factorisation method's arithmetic lives here.
+"""
+from .ratings import (  # noqa: F401
+    Ratings, CONFIGS, make_config, make_ratings, init_factors, rank_degrees,
+    sample_distinct, half_star_values, make_dense, foldin_requests,
+)

@@ -1,0 +1,338 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix
+(no GPU).  Each test names the passage it follows."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _small_problem(n_u=40, n_m=25, n_f=4, lam=0.05, dens=0.3, seed=7, min_deg=1):
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n_u, n_m)) < dens
+    for i in range(n_u):                      # every user rates >= min_deg items
+        if mask[i].sum() < min_deg:
+            mask[i, rng.choice(n_m, min_deg, replace=False)] = True
+    for j in range(n_m):
+        if mask[:, j].sum() < min_deg:
+            mask[rng.choice(n_u, min_deg, replace=False), j] = True
+    rows, cols = np.nonzero(mask)
+    vals = np.round(2 * np.clip(rng.normal(3.5, 1.0, rows.shape[0]), 0.5, 5)) / 2
+    P = oracle.build_problem(n_u, n_m, n_f, lam, rows, cols, vals)
+    x0 = synth.init_factors(n_u, n_m, n_f, seed + 100)
+    return P, x0
+
+
+# -- per-row solve -----------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 10, 37, 100])
+def test_chol_solve_matches_lapack(n):
+    """Eq. (3)/(4) are solved by Cholesky (§V-B); the textbook factorisation
+    must agree with LAPACK's general solver on SPD systems."""
+    rng = np.random.default_rng(n)
+    B = rng.normal(size=(n, 2 * n + 3))
+    A = B @ B.T + 0.1 * np.eye(n)
+    b = rng.normal(size=n)
+    x = oracle.chol_solve(A, b)
+    ref = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref) * np.linalg.cond(A) ** 0.5
+
+
+def test_chol_rejects_indefinite():
+    A = np.array([[1.0, 2.0], [2.0, 1.0]])
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.chol_solve(A, np.ones(2))
+
+
+def test_user_solve_is_ridge_least_squares():
+    """Eq. (3): u_i minimises sum_j (r_ij - u.m_j)^2 + lambda n_ui |u|^2, i.e.
+    the stacked least-squares problem [M_I^T; sqrt(lambda n) I] u = [r; 0]."""
+    P, x0 = _small_problem()
+    M = x0[P.n_u * P.n_f:].reshape(P.n_m, P.n_f)
+    U = oracle.half_sweep(P, 0, M).reshape(P.n_u, P.n_f)
+    for i in range(P.n_u):
+        a, b = P.uptr[i], P.uptr[i + 1]
+        MI = M[P.uidx[a:b]]
+        n = b - a
+        S = np.vstack([MI, np.sqrt(P.lam * n) * np.eye(P.n_f)])
+        rhs = np.concatenate([P.uval[a:b], np.zeros(P.n_f)])
+        ref = np.linalg.lstsq(S, rhs, rcond=None)[0]
+        assert np.allclose(U[i], ref, rtol=1e-11, atol=1e-12)
+
+
+def test_item_solve_is_ridge_least_squares():
+    """Eq. (4), the item-side analogue."""
+    P, x0 = _small_problem(seed=9)
+    U = x0[:P.n_u * P.n_f].reshape(P.n_u, P.n_f)
+    M = oracle.half_sweep(P, 1, U).reshape(P.n_m, P.n_f)
+    for j in range(P.n_m):
+        a, b = P.mptr[j], P.mptr[j + 1]
+        UI = U[P.midx[a:b]]
+        n = b - a
+        S = np.vstack([UI, np.sqrt(P.lam * n) * np.eye(P.n_f)])
+        rhs = np.concatenate([P.mval[a:b], np.zeros(P.n_f)])
+        ref = np.linalg.lstsq(S, rhs, rcond=None)[0]
+        assert np.allclose(M[j], ref, rtol=1e-11, atol=1e-12)
+
+
+def test_empty_rows_are_held_at_zero():
+    """An item nobody rated does not enter f; its solve gives 0, its gradient 0."""
+    rows = np.array([0, 0, 1]); cols = np.array([0, 1, 1]); vals = np.array([4.0, 3.0, 5.0])
+    P = oracle.build_problem(2, 3, 2, 0.1, rows, cols, vals)
+    x = synth.init_factors(2, 3, 2, 5)
+    xb = oracle.sweep(P, x)
+    assert np.all(xb[(2 + 2) * 2:] == 0.0)
+    g = oracle.grad(P, xb)
+    assert np.all(g[(2 + 2) * 2:] == 0.0)
+
+
+# -- half-sweeps and ALS (Algorithm 1) -----------------------------------------
+
+def test_half_sweeps_zero_block_gradient():
+    """§III-A: the U half sets dL/du_i = 0 for every i (closed-form normal
+    equations); the M half does the same for every m_j."""
+    P, x = _small_problem(n_u=60, n_m=30, n_f=5)
+    k = P.n_u * P.n_f
+    g0 = oracle.grad(P, x)
+    xu = x.copy()
+    xu[:k] = oracle.half_sweep(P, 0, x[k:])
+    gu = oracle.grad(P, xu)
+    assert np.linalg.norm(gu[:k]) <= 1e-10 * np.linalg.norm(g0[:k])
+    xm = xu.copy()
+    xm[k:] = oracle.half_sweep(P, 1, xu[:k])
+    gm = oracle.grad(P, xm)
+    assert np.linalg.norm(gm[k:]) <= 1e-10 * np.linalg.norm(g0[k:])
+
+
+def test_als_decreases_f_every_half_sweep():
+    """Each half of Algorithm 1 is an exact block minimisation, so f never rises."""
+    r = synth.make_config("tiny")
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    x = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    k = P.n_u * P.n_f
+    f = oracle.loss(P, x)
+    for _ in range(4):
+        x = x.copy(); x[:k] = oracle.half_sweep(P, 0, x[k:])
+        f1 = oracle.loss(P, x)
+        assert f1 <= f * (1 + 1e-13)
+        x = x.copy(); x[k:] = oracle.half_sweep(P, 1, x[:k])
+        f2 = oracle.loss(P, x)
+        assert f2 <= f1 * (1 + 1e-13)
+        f = f2
+
+
+def test_sweep_is_the_two_halves():
+    """P(x) = U half from x's M block, then M half from the new U (Algorithm 1)."""
+    P, x = _small_problem()
+    k = P.n_u * P.n_f
+    xb = oracle.sweep(P, x)
+    U = oracle.half_sweep(P, 0, x[k:])
+    M = oracle.half_sweep(P, 1, U)
+    assert np.array_equal(xb, np.concatenate([U, M]))
+
+
+# -- loss and gradient -----------------------------------------------------------
+
+def test_loss_special_values():
+    """Eq. (1) at U = M = 0 is sum r^2; a planted exact fit with lambda = 0 gives 0."""
+    P, x = _small_problem(lam=0.3)
+    assert oracle.loss(P, np.zeros_like(x)) == pytest.approx(np.sum(P.uval ** 2), rel=1e-14)
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=(6, 2)); M = rng.normal(size=(5, 2))
+    rows, cols = np.meshgrid(np.arange(6), np.arange(5), indexing="ij")
+    rows, cols = rows.ravel(), cols.ravel()
+    vals = np.einsum("ij,ij->i", U[rows], M[cols])
+    Q = oracle.build_problem(6, 5, 2, 0.0, rows, cols, vals)
+    assert abs(oracle.loss(Q, np.concatenate([U.ravel(), M.ravel()]))) < 1e-25 + 1e-14 * np.sum(vals ** 2)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gradient_matches_finite_differences(seed):
+    """The gradient of §V-C equals central differences of Eq. (1)."""
+    P, x = _small_problem(n_u=7, n_m=6, n_f=3, lam=0.2, dens=0.5, seed=seed)
+    g = oracle.grad(P, x)
+    h = 1e-6
+    fd = np.empty_like(x)
+    for t in range(x.shape[0]):
+        e = np.zeros_like(x); e[t] = h
+        fd[t] = (oracle.loss(P, x + e) - oracle.loss(P, x - e)) / (2 * h)
+    assert np.linalg.norm(g - fd) <= 1e-6 * np.linalg.norm(g)
+
+
+# -- line-search polynomial (§V-C) -------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 4])
+def test_quartic_reproduces_loss(seed):
+    """Q(alpha) = f(x + alpha p) for every alpha; c0 = f(x), c1 = g^T p, c4 >= 0."""
+    P, x = _small_problem(n_u=50, n_m=30, n_f=6, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    p = rng.normal(size=x.shape[0]) * 0.3
+    c = oracle.ls_coeffs(P, x, p)
+    for a in (-1.0, 0.0, 0.3, 1.0, 2.5):
+        f = oracle.loss(P, x + a * p)
+        assert oracle.q_eval(c, a) == pytest.approx(f, rel=1e-12)
+    assert c[0] == pytest.approx(oracle.loss(P, x), rel=1e-13)
+    assert c[1] == pytest.approx(float(oracle.grad(P, x) @ p), rel=1e-11)
+    assert c[4] >= 0.0
+    # Vandermonde: five samples of f determine the quartic exactly
+    al = np.array([-1.0, -0.4, 0.2, 0.7, 1.3])
+    V = np.vander(al, 5, increasing=True)
+    coef = np.linalg.solve(V, [oracle.loss(P, x + a * p) for a in al])
+    assert np.allclose(coef, c, rtol=1e-7, atol=1e-9 * abs(c[0]))
+
+
+def test_backtracking_armijo_invariants():
+    """Algorithm 3 on Q: the accepted alpha passes the sufficient-decrease test,
+    alpha / tau did not, and alpha = alpha0 tau^k."""
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        c = np.array([5.0, -abs(rng.normal()) - 1e-3, rng.normal(), rng.normal(), abs(rng.normal()) + 1e-6])
+        ls = oracle.backtracking(c)
+        assert ls.ok
+        dq = lambda a: oracle.q_eval(c, a) - c[0]
+        assert dq(ls.alpha) <= ls.alpha * 0.5 * c[1] * (1 - 1e-12)
+        assert ls.alpha == pytest.approx(10.0 * 0.9 ** ls.shrinks, rel=1e-12)
+        if ls.shrinks > 0:
+            a_prev = ls.alpha / 0.9
+            assert dq(a_prev) > a_prev * 0.5 * c[1] * (1 + 1e-12)
+    assert not oracle.backtracking(np.array([1.0, 0.5, 1.0, 0.0, 1.0])).ok
+
+
+def test_exact_step_minimises_quartic():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        c = np.array([3.0, -abs(rng.normal()) - 0.1, rng.normal(), rng.normal(), abs(rng.normal()) + 0.05])
+        ls = oracle.exact_step(c)
+        grid = np.linspace(1e-6, 50, 200001)
+        qv = c[0] + grid * (c[1] + grid * (c[2] + grid * (c[3] + grid * c[4])))
+        assert oracle.q_eval(c, ls.alpha) <= qv.min() + 1e-9 * abs(qv.min())
+
+
+# -- Algorithm 2 ---------------------------------------------------------------------
+
+def test_ncg_wrapper_reproduces_pcg():
+    """§III-B: on f = x^T A x / 2 - b^T x with a linear preconditioner
+    P(x) = x - B (A x - b) and an exact line search, Algorithm 2 with beta of
+    Eq. (8) is preconditioned CG (textbook form, Nocedal & Wright Alg. 5.3)."""
+    n = 12
+    rng = np.random.default_rng(5)
+    Q = rng.normal(size=(n, n)); A = Q @ Q.T + n * np.eye(n)
+    C = rng.normal(size=(n, n)); B = np.linalg.inv(C @ C.T + n * np.eye(n))
+    b = rng.normal(size=n); x0 = rng.normal(size=n)
+    iters = []
+
+    def step(x, p, g):
+        return oracle.core.LineSearchResult(float(-(g @ p) / (p @ A @ p)), True, 0, np.inf)
+
+    oracle.ncg(x0, lambda x: A @ x - b, lambda x: x - B @ (A @ x - b), step, n,
+               on_iter=lambda k, x, g, info: iters.append(x.copy()))
+    # textbook PCG
+    x = x0.copy(); r = A @ x - b; y = B @ r; p = -y
+    ref = []
+    for _ in range(n):
+        a = (r @ y) / (p @ A @ p)
+        x = x + a * p
+        r1 = r + a * A @ p
+        y1 = B @ r1
+        beta = (r1 @ y1) / (r @ y)
+        p = -y1 + beta * p
+        r, y = r1, y1
+        ref.append(x.copy())
+    xs = np.linalg.solve(A, b)
+    for k in range(n):
+        assert np.linalg.norm(iters[k] - ref[k]) <= 1e-10 * np.linalg.norm(xs)
+    assert np.linalg.norm(iters[-1] - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def _dense_minimum(R, n_f, lam):
+    """Global minimum of Eq. (1) when every rating is observed:
+    f = |R - U^T M|_F^2 + a|U|^2 + b|M|^2 with a = lam n_m, b = lam n_u;
+    min over U^T M = Z of a|U|^2 + b|M|^2 is 2 sqrt(ab) |Z|_*, so the optimum
+    soft-thresholds the top n_f singular values by s = sqrt(ab)."""
+    n_u, n_m = R.shape
+    s = np.sqrt(lam * n_m * lam * n_u)
+    sig = np.linalg.svd(R, compute_uv=False)
+    top, rest = sig[:n_f], sig[n_f:]
+    val = np.where(top > s, 2 * s * top - s * s, top ** 2).sum() + (rest ** 2).sum()
+    return val
+
+
+def test_als_and_alsncg_reach_dense_global_minimum():
+    """Closed form: on a fully observed 30 x 20 R, both Algorithm 1 and
+    Algorithm 2 must reach the global minimum of Eq. (1)."""
+    rows, cols, vals = synth.make_dense(30, 20, 3, seed=4)
+    P = oracle.build_problem(30, 20, 3, 0.05, rows, cols, vals)
+    fstar = _dense_minimum(vals.reshape(30, 20), 3, 0.05)
+    x0 = synth.init_factors(30, 20, 3, 8)
+    ra = oracle.als(P, x0, 400, keep_x=False, with_grad=False)
+    assert ra[-1].f == pytest.approx(fstar, rel=1e-8)
+    rn = oracle.alsncg(P, x0, 60, keep_x=False)
+    assert rn[-1].f == pytest.approx(fstar, rel=1e-8)
+    assert rn[-1].f >= fstar * (1 - 1e-12)
+
+
+def test_tiny_brute_force_fixed_point():
+    """n_f = 1, a 3 x 2 R with one missing rating: the ALS fixed point is the
+    minimum found by a grid search over all five unknowns plus a local polish."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    rows = np.array([0, 0, 1, 1, 2]); cols = np.array([0, 1, 0, 1, 0])
+    vals = np.array([4.0, 2.0, 3.5, 1.0, 5.0])
+    P = oracle.build_problem(3, 2, 1, 0.1, rows, cols, vals)
+    g = np.linspace(-3, 3, 25)
+    G = np.stack(np.meshgrid(g, g, g, g, g, indexing="ij"), -1).reshape(-1, 5)
+    u, m = G[:, :3], G[:, 3:]
+    f = np.zeros(G.shape[0])
+    for r_, c_, v_ in zip(rows, cols, vals):
+        f += (v_ - u[:, r_] * m[:, c_]) ** 2
+    nu = np.bincount(rows, minlength=3); nm = np.bincount(cols, minlength=2)
+    f += 0.1 * ((nu * u ** 2).sum(1) + (nm * m ** 2).sum(1))
+    best = G[np.argmin(f)]
+    res = scipy_opt.minimize(lambda x: oracle.loss(P, x), best, jac=lambda x: oracle.grad(P, x),
+                             method="BFGS", options=dict(gtol=1e-12, maxiter=500))
+    x = np.array([0.5, 0.5, 0.5, 1.0, 1.0])
+    for _ in range(2000):
+        x = oracle.sweep(P, x)
+    assert oracle.loss(P, x) == pytest.approx(res.fun, rel=1e-8)
+
+
+def test_foldin_equals_user_half_sweep_row():
+    """Fold-in is Eq. (3) for a row given from outside R: feeding an existing
+    user's ratings gives that user's half-sweep row."""
+    P, x = _small_problem(n_u=30, n_m=20, n_f=4)
+    k = P.n_u * P.n_f
+    U = oracle.half_sweep(P, 0, x[k:]).reshape(P.n_u, P.n_f)
+    users = [0, 5, 17]
+    ptr = np.concatenate([[0], np.cumsum([P.uptr[i + 1] - P.uptr[i] for i in users])])
+    items = np.concatenate([P.uidx[P.uptr[i]:P.uptr[i + 1]] for i in users])
+    vals = np.concatenate([P.uval[P.uptr[i]:P.uptr[i + 1]] for i in users])
+    out = oracle.foldin(P.n_f, P.lam, x[k:], ptr, items, vals)
+    assert np.allclose(out, U[users], rtol=1e-13, atol=1e-14)
+
+
+def test_alsncg_beats_als_on_tiny():
+    """§IV: on the same x_0, ALS-NCG reaches a lower gradient norm than ALS in
+    the same number of iterations (the acceleration the paper reports)."""
+    r = synth.make_config("tiny")
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    ra = oracle.als(P, x0, 50, keep_x=False)
+    rn = oracle.alsncg(P, x0, 50, keep_x=False)
+    assert rn[-1].gnorm < ra[-1].gnorm
+    assert rn[-1].f <= ra[-1].f * (1 + 1e-9)
+
+
+def test_thread_count_does_not_change_results():
+    r = synth.make_config("tiny")
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    n0 = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        a = (oracle.loss(P, x0), oracle.grad(P, x0), oracle.sweep(P, x0), oracle.ls_coeffs(P, x0, x0))
+        oracle.set_threads(4)
+        b = (oracle.loss(P, x0), oracle.grad(P, x0), oracle.sweep(P, x0), oracle.ls_coeffs(P, x0, x0))
+    finally:
+        oracle.set_threads(n0)
+    assert a[0] == b[0]
+    for u, v in zip(a[1:], b[1:]):
+        assert np.array_equal(u, v)
