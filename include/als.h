@@ -1,0 +1,209 @@
+/*
+ * als.h -- C ABI of the GB300 (sm_103a) ALS-WR / ALS-NCG library.
+ *
+ * The method is Winlaw, Hynes, Caterini, De Sterck, "Algorithmic Acceleration
+ * of Parallel ALS for Collaborative Filtering" (arXiv 1508.03110):
+ * regularised low-rank factorisation R ~ U^T M of a sparse ratings matrix by
+ * ALS sweeps (Algorithm 1) used as the nonlinear preconditioner of a
+ * nonlinear conjugate gradient method (Algorithm 2), with a line search
+ * (Algorithm 3) run on the quartic Q(alpha) = f(x + alpha p) whose
+ * coefficients come from one pass over the ratings (§V-C).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Factors.  U is n_u x n_f and M is n_m x n_f, row-major, one row per user /
+ *   item (row i of U is the column u_i of the paper's U in R^{n_f x n_u}).  The
+ *   iterate x of Eq. (5) is [u_1 .. u_{n_u}, m_1 .. m_{n_m}].
+ * dtype.  ALS_DT_F64 (double) or ALS_DT_F32 (float) for factor / vector
+ *   buffers the caller passes in or out.  Conversion happens on the device.
+ * on_device.  Non-zero: the pointer is CUDA device memory (or managed memory)
+ *   valid on the context's device; zero: it is host memory.  Host buffers are
+ *   copied inside the call (pageable or pinned both work).
+ * Ownership.  Inputs are copied; the caller keeps ownership of every buffer it
+ *   passes.  The context owns all device memory it allocates until
+ *   als_destroy().
+ * Streams.  Every call enqueues its work on the stream given to als_create()
+ *   and returns after enqueueing, except calls that return host values (they
+ *   synchronise that stream first).  NULL: the context creates and owns a
+ *   non-blocking stream (the legacy default stream cannot be captured into
+ *   the CUDA graphs alsncg_run replays); order other work with als_sync().
+ * Errors.  Every call returns an als_status; on failure the context stays
+ *   valid, the iterate is unchanged, and als_last_error() returns a
+ *   thread-local message.  Nothing throws across the ABI.  A failed CUDA call
+ *   returns ALS_ECUDA.
+ * Precision.  ALS_FP64 computes everything in double (parity form).
+ *   ALS_MIXED stores factors and NCG vectors in float, builds the Gram
+ *   matrices in BF16 on the tensor cores (n_f > 64) or in FP32 (n_f <= 64),
+ *   factors them in FP32 and corrects each solve by iterative refinement
+ *   against an FP32 residual; f, |g|, the beta inner products and the Q
+ *   coefficients are reduced in FP64.
+ * Determinism.  Reductions use a fixed order and no floating-point atomics:
+ *   repeated runs on the same device give bit-identical results.
+ * Sizes.  1 <= n_f <= 128; n_u, n_m < 2^31; nnz < 2^40.
+ */
+#ifndef ALS_H
+#define ALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ALS_API __attribute__((visibility("default")))
+#else
+#define ALS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct als_ctx als_ctx;
+
+typedef enum {
+    ALS_OK = 0,
+    ALS_EINVAL = 1,       /* bad argument or malformed ratings            */
+    ALS_ENOMEM = 2,       /* device allocation failed                     */
+    ALS_EBUDGET = 3,      /* allocation would exceed hbm_budget_bytes     */
+    ALS_ECUDA = 4,        /* a CUDA runtime call failed                   */
+    ALS_ENOTSPD = 5,      /* a row system was not positive definite       */
+    ALS_ELINESEARCH = 6,  /* reserved: line search failures fall back     */
+    ALS_ETIMEOUT = 7,     /* a bounded device wait ran out                */
+    ALS_EBUSY = 8,        /* the context is in use by another call        */
+    ALS_ENOTSUP = 9       /* configuration not supported on this device   */
+} als_status;
+
+typedef enum { ALS_FP64 = 0, ALS_MIXED = 1 } als_precision;
+typedef enum { ALS_LS_BACKTRACK = 0, ALS_LS_EXACT = 1 } als_ls_mode;
+typedef enum { ALS_DT_F64 = 0, ALS_DT_F32 = 1 } als_dtype;
+typedef enum { ALS_GRAM_AUTO = 0, ALS_GRAM_FMA = 1, ALS_GRAM_TC = 2 } als_gram_path;
+
+/* Optional allocator hooks (e.g. a framework's caching allocator).  alloc
+ * returns device memory of at least `bytes` (256-byte aligned) or NULL;
+ * free releases it.  Both may be NULL: cudaMalloc / cudaFree are used. */
+typedef void *(*als_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*als_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+    int32_t n_f;              /* number of latent factors, 1..128            */
+    double lambda;            /* weighted-lambda regularisation, Eq. (1)      */
+    int32_t precision;        /* als_precision                                */
+    int32_t ls_mode;          /* als_ls_mode                                  */
+    double ls_alpha0;         /* Algorithm 3 start step (paper: 10)          */
+    double ls_tau;            /* Algorithm 3 shrink factor (paper: 0.9)      */
+    double ls_c;              /* Algorithm 3 sufficient decrease (paper: 0.5)*/
+    int32_t ls_max_shrinks;   /* shrink limit before the ALS fallback (200)  */
+    int32_t refine_steps;     /* ALS_MIXED: residual corrections per solve   */
+    int32_t gram_path;        /* als_gram_path                                */
+    size_t hbm_budget_bytes;  /* 0 = no limit                                 */
+    als_alloc_fn alloc;
+    als_free_fn free;
+    void *alloc_user;
+} als_config;
+
+/* Per-iteration record of Algorithm 2. */
+typedef struct {
+    int64_t k;          /* iterations completed                              */
+    double f;           /* f(x_k): Q(alpha) of the accepted step, or the
+                           evaluated loss after a fallback step             */
+    double gnorm;       /* |g_k| = |grad f(x_k)| (FP64)                       */
+    double gnorm0;      /* |g_0|                                              */
+    double alpha;       /* accepted step length (0 after a fallback)         */
+    double beta;        /* beta-bar of Eq. (8) used for p_k                  */
+    double c[5];        /* Q coefficients of the step that produced x_k      */
+    int32_t shrinks;    /* Algorithm 3 backtracking count                    */
+    int32_t fallback;   /* 1: the step took the ALS point (no descent / no
+                           alpha passed); the direction restarted            */
+    int64_t fallbacks;  /* total fallbacks so far                            */
+    int64_t notspd;     /* rows whose system was not SPD so far              */
+} als_iter_info;
+
+/* Fill *cfg with the paper's defaults: alpha0 = 10, tau = 0.9, c = 0.5
+ * (§V-C), 200 shrinks, backtracking, FP64, one refinement step, auto Gram. */
+ALS_API void als_config_default(als_config *cfg);
+
+/* Build a context from ratings (§II, §V-B: R is stored twice, by user and by
+ * item).  COO when rowptr_or_null == NULL (rows_or_null[nnz] user ids), else
+ * CSR (rowptr_or_null[n_u+1], rows_or_null ignored).  cols[nnz] item ids,
+ * vals[nnz] ratings.  Validates ids in range, finite values and no duplicate
+ * (user, item) pair (ALS_EINVAL otherwise).  The device then builds the
+ * by-user CSR, the by-item CSC and degree-ordered row lists.  Factors start at
+ * zero: call als_set_factors() before iterating.  Synchronous. */
+ALS_API als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
+                      const int32_t *rows_or_null, const int64_t *rowptr_or_null,
+                      const int32_t *cols, const float *vals, int on_device,
+                      void *cuda_stream, als_ctx **out);
+
+/* Inspection of what the device builder made (§V-B storage), copied to host
+ * arrays; any pointer may be NULL.  uptr[n_u+1] / uidx[nnz] / uval[nnz]: by
+ * user, items ascending; mptr[n_m+1] / midx[nnz] / mval[nnz]: by item, users
+ * ascending; uorder[n_u] / morder[n_m]: ids by descending degree, ties by
+ * ascending id.  Synchronous. */
+ALS_API als_status als_get_ratings(als_ctx *ctx, int64_t *uptr, int32_t *uidx, float *uval, int64_t *mptr,
+                           int32_t *midx, float *mval, int32_t *uorder, int32_t *morder);
+
+/* Set x (Eq. 5) from U (n_u x n_f) and M (n_m x n_f) of the given dtype.
+ * Resets the ALS-NCG state (the next alsncg_step starts Algorithm 2 anew). */
+ALS_API als_status als_set_factors(als_ctx *ctx, const void *U, const void *M, int dtype,
+                           int on_device);
+
+/* Copy x out into U (n_u x n_f) and M (n_m x n_f).  Synchronous for host
+ * destinations. */
+ALS_API als_status als_get_factors(als_ctx *ctx, void *U, void *M, int dtype, int on_device);
+
+/* Algorithm 1: n_sweeps times x <- P(x): all u_i by Eq. (3) from M, then all
+ * m_j by Eq. (4) from the new U.  Asynchronous. */
+ALS_API als_status als_sweep(als_ctx *ctx, int32_t n_sweeps);
+
+/* One iteration of Algorithm 2 (ALS-NCG).  The first call after
+ * als_set_factors() also performs its initialisation (g_0, gbar_0 = x_0 -
+ * P(x_0), p_0 = -gbar_0).  If out != NULL the call synchronises and fills
+ * *out; otherwise it is asynchronous. */
+ALS_API als_status alsncg_step(als_ctx *ctx, als_iter_info *out);
+
+/* Repeat Algorithm 2 until |g_k| <= rel_tol * |g_0| or max_iter iterations,
+ * reading |g_k| back every check_every iterations (iterations run as CUDA
+ * graph replays).  *iters_done = iterations run in this call.  Synchronous. */
+ALS_API als_status alsncg_run(als_ctx *ctx, int32_t max_iter, double rel_tol, int32_t check_every,
+                      als_iter_info *last, int32_t *iters_done);
+
+/* f(x) of Eq. (1), reduced in FP64.  Synchronous. */
+ALS_API als_status als_loss(als_ctx *ctx, double *f);
+
+/* Gradient of Eq. (1) at x (§V-C "Gradient Evaluation").  g_out_or_null
+ * receives n_u + n_m rows of n_f (dtype, on_device); gnorm (nullable)
+ * receives |g| in FP64.  Synchronous when gnorm or a host g_out is given. */
+ALS_API als_status als_grad(als_ctx *ctx, void *g_out_or_null, int dtype, int on_device,
+                    double *gnorm);
+
+/* The five coefficients of Q(alpha) = f(x + alpha p) = sum c_n alpha^n
+ * (§V-C), from one pass over the ratings, in FP64.  p_or_null: a direction of
+ * n_u + n_m rows of n_f (dtype, on_device); NULL uses the context's current
+ * ALS-NCG direction p_k.  Synchronous. */
+ALS_API als_status als_linesearch_coeffs(als_ctx *ctx, const void *p_or_null, int dtype,
+                                 int on_device, double c[5]);
+
+/* Fold-in: for each of n_req new users with ratings items/vals[req_ptr[q] ..
+ * req_ptr[q+1]) solve Eq. (3) against the context's current M, i.e.
+ * u = (M_I M_I^T + lambda |I| I)^-1 M_I r.  u_out: n_req x n_f (dtype,
+ * on_device).  Empty requests give u = 0.  Synchronous for host output. */
+ALS_API als_status als_foldin(als_ctx *ctx, int64_t n_req, const int64_t *req_ptr,
+                      const int32_t *items, const float *vals, int on_device_in,
+                      void *u_out, int dtype, int on_device_out);
+
+/* Wait for all work enqueued by this context. */
+ALS_API als_status als_sync(als_ctx *ctx);
+
+/* Release everything the context owns.  NULL is ignored. */
+ALS_API void als_destroy(als_ctx *ctx);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+ALS_API const char *als_last_error(void);
+
+/* Library build string (architecture, version). */
+ALS_API const char *als_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALS_H */

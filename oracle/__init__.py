@@ -18,9 +18,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   als / alsncg    pinned: reach the closed-form global minimum of a fully
                   observed problem; ALS decreases f monotonically
   foldin          pinned: equals the user half-sweep row for a user already in R
+  solve_rows      pinned: equals the selected rows of half_sweep
 """
 from .core import (  # noqa: F401
-    Problem, build_problem, loss, grad, half_sweep, sweep, ls_coeffs, chol_solve,
+    Problem, build_problem, loss, grad, half_sweep, solve_rows, sweep, ls_coeffs, chol_solve,
     foldin, q_eval, backtracking, exact_step, ncg, als, alsncg, set_threads,
     get_threads, IterRecord,
 )

@@ -225,6 +225,30 @@ int64_t orc_half_sweep(const orc_problem *P, int side, const double *F, double *
     return bad;
 }
 
+/* The same solve for a chosen subset of rows only (rows[q] of side 0/1);
+ * OUT[q] receives that row.  Used to check sampled rows of large problems. */
+int64_t orc_solve_rows(const orc_problem *P, int side, const double *F, int64_t nsel,
+                       const int64_t *rows, double *OUT) {
+    const int nf = P->n_f;
+    const int64_t *ptr = side == 0 ? P->uptr : P->mptr;
+    const int32_t *idx = side == 0 ? P->uidx : P->midx;
+    const double *val = side == 0 ? P->uval : P->mval;
+    int64_t bad = 0;
+#pragma omp parallel reduction(+ : bad)
+    {
+        double *work = (double *)malloc(sizeof(double) * (size_t)(2 * nf * nf + nf));
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < nsel; ++q) {
+            const int64_t i = rows[q];
+            if (orc_solve_row(nf, P->lambda, ptr[i + 1] - ptr[i], idx + ptr[i], val + ptr[i], F,
+                              OUT + q * nf, work) != 0)
+                bad += 1;
+        }
+        free(work);
+    }
+    return bad;
+}
+
 /* P(x) = one ALS iteration, Algorithm 1 loop body: the U block of XBAR from
  * the M block of X, then the M block of XBAR from the new U block. */
 int64_t orc_sweep(const orc_problem *P, const double *X, double *XBAR) {

@@ -48,6 +48,7 @@ def _load():
     lib.orc_ls_coeffs.argtypes = [P, vp, vp, vp]; lib.orc_ls_coeffs.restype = None
     lib.orc_chol_solve.argtypes = [i32, vp, vp, vp, vp]; lib.orc_chol_solve.restype = i32
     lib.orc_foldin.argtypes = [i32, dbl, i64, vp, vp, vp, vp, vp]; lib.orc_foldin.restype = i64
+    lib.orc_solve_rows.argtypes = [P, i32, vp, i64, vp, vp]; lib.orc_solve_rows.restype = i64
     lib.orc_set_threads.argtypes = [i32]; lib.orc_set_threads.restype = None
     lib.orc_get_threads.argtypes = []; lib.orc_get_threads.restype = i32
     _lib = lib
@@ -150,6 +151,17 @@ def half_sweep(P: Problem, side: int, F) -> np.ndarray:
     if bad:
         raise FloatingPointError(f"{bad} rows not positive definite")
     return out
+
+
+def solve_rows(P: Problem, side: int, F, rows) -> np.ndarray:
+    """Eq. (3) (side 0) or Eq. (4) (side 1) for the selected rows only."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(rows.shape[0] * P.n_f, np.float64)
+    bad = _load().orc_solve_rows(P.cstruct(), int(side), _ptr(F), rows.shape[0], _ptr(rows), _ptr(out))
+    if bad:
+        raise FloatingPointError(f"{bad} rows not positive definite")
+    return out.reshape(rows.shape[0], P.n_f)
 
 
 def sweep(P: Problem, x) -> np.ndarray:

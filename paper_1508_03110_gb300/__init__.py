@@ -1,0 +1,242 @@
+"""GB300-native ALS-WR / ALS-NCG (arXiv 1508.03110) behind a C ABI.
+
+The Python layer only marshals arguments to the entry points declared in
+include/als.h; every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory (its caching allocator is passed to
+the library as the allocation hook) and the CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ALS_FP64, ALS_MIXED, ALS_LS_BACKTRACK, ALS_LS_EXACT, ALS_DT_F64, ALS_DT_F32,  # noqa: F401
+                   ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC, ALSError, IterInfo)
+
+__all__ = ["ALS", "ALSError", "load", "info_dict"]
+
+
+def load():
+    return _lib.load()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def info_dict(info: IterInfo) -> dict:
+    return dict(k=info.k, f=info.f, gnorm=info.gnorm, gnorm0=info.gnorm0, alpha=info.alpha,
+                beta=info.beta, c=list(info.c), shrinks=info.shrinks, fallback=bool(info.fallback),
+                fallbacks=info.fallbacks, notspd=info.notspd)
+
+
+class _Buf:
+    """A host (numpy) or device (torch) buffer handed to the C ABI."""
+
+    def __init__(self, arr, np_dtype):
+        torch = _torch()
+        if isinstance(arr, torch.Tensor):
+            want = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+                    np.int64: torch.int64}[np_dtype]
+            t = arr.contiguous()
+            if t.dtype != want:
+                t = t.to(want)
+            self.keep = t
+            self.ptr = t.data_ptr()
+            self.on_device = 1 if t.is_cuda else 0
+        else:
+            a = np.ascontiguousarray(arr, dtype=np_dtype)
+            self.keep = a
+            self.ptr = a.ctypes.data
+            self.on_device = 0
+
+
+class ALS:
+    """One factorisation problem R ~ U^T M on the current CUDA device.
+
+    precision: "fp64" (parity form) or "mixed" (BF16/FP32 Gram, FP32
+    Cholesky with refinement, FP64 reductions).
+    """
+
+    def __init__(self, n_u, n_m, rows, cols, vals, n_f, lam, precision="fp64", ls_mode="backtrack",
+                 refine_steps=1, gram_path="auto", hbm_budget_bytes=0, stream=None, rowptr=None,
+                 ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.n_u, self.n_m, self.n_f = int(n_u), int(n_m), int(n_f)
+        cfg = _lib.Config()
+        self.lib.als_config_default(ctypes.byref(cfg))
+        cfg.n_f = self.n_f
+        cfg.lam = float(lam)
+        cfg.precision = {"fp64": ALS_FP64, "mixed": ALS_MIXED}[precision]
+        cfg.ls_mode = {"backtrack": ALS_LS_BACKTRACK, "exact": ALS_LS_EXACT}[ls_mode]
+        cfg.ls_alpha0, cfg.ls_tau, cfg.ls_c = float(ls_alpha0), float(ls_tau), float(ls_c)
+        cfg.ls_max_shrinks = int(ls_max_shrinks)
+        cfg.refine_steps = int(refine_steps)
+        cfg.gram_path = {"auto": ALS_GRAM_AUTO, "fma": ALS_GRAM_FMA, "tc": ALS_GRAM_TC}[gram_path]
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        # device memory comes from torch's caching allocator
+        self._blocks = {}
+
+        def _alloc(nbytes, stream_, user):
+            dev = torch.cuda.current_device()
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream_ or 0)
+            return ptr
+
+        def _free(ptr, nbytes, stream_, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = _lib.ALLOC_FN(_alloc)
+        self._free_cb = _lib.FREE_FN(_free)
+        cfg.alloc = self._alloc_cb
+        cfg.free = self._free_cb
+        self.cfg = cfg
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nnz = int(len(cols))
+        self.nnz = nnz
+        cb = _Buf(cols, np.int32)
+        vb = _Buf(vals, np.float32)
+        if rowptr is not None:
+            rp = _Buf(rowptr, np.int64)
+            rb_ptr, rp_ptr = None, rp.ptr
+            on_dev = rp.on_device
+        else:
+            rb = _Buf(rows, np.int32)
+            rb_ptr, rp_ptr = rb.ptr, None
+            on_dev = rb.on_device
+        if not (cb.on_device == vb.on_device == on_dev):
+            raise ValueError("ratings arrays must all be on the host or all on the device")
+        ctx = ctypes.c_void_p()
+        st = self.lib.als_create(ctypes.byref(cfg), self.n_u, self.n_m, nnz, rb_ptr, rp_ptr, cb.ptr,
+                                 vb.ptr, on_dev, ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(ctx))
+        _lib.check(st, "als_create")
+        self.ctx = ctx
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.als_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def ratings(self):
+        """The device-built by-user / by-item structures and degree orders."""
+        nnz = self.nnz
+        out = dict(uptr=np.empty(self.n_u + 1, np.int64), uidx=np.empty(nnz, np.int32),
+                   uval=np.empty(nnz, np.float32), mptr=np.empty(self.n_m + 1, np.int64),
+                   midx=np.empty(nnz, np.int32), mval=np.empty(nnz, np.float32),
+                   uorder=np.empty(self.n_u, np.int32), morder=np.empty(self.n_m, np.int32))
+        _lib.check(self.lib.als_get_ratings(self.ctx, *[out[k].ctypes.data for k in
+                                                        ("uptr", "uidx", "uval", "mptr", "midx", "mval",
+                                                         "uorder", "morder")]), "als_get_ratings")
+        return out
+
+    # -- factors ----------------------------------------------------------------
+    def set_factors(self, U, M):
+        dt = ALS_DT_F64
+        if not isinstance(U, np.ndarray) and getattr(U, "dtype", None) is not None and "float32" in str(U.dtype):
+            dt = ALS_DT_F32
+        npdt = np.float64 if dt == ALS_DT_F64 else np.float32
+        ub, mb = _Buf(U, npdt), _Buf(M, npdt)
+        if ub.on_device != mb.on_device:
+            raise ValueError("U and M must both be on the host or both on the device")
+        _lib.check(self.lib.als_set_factors(self.ctx, ub.ptr, mb.ptr, dt, ub.on_device), "als_set_factors")
+        if ub.on_device:
+            self.sync()
+
+    def set_x(self, x):
+        x = np.asarray(x, np.float64).reshape(self.n_u + self.n_m, self.n_f)
+        self.set_factors(x[:self.n_u], x[self.n_u:])
+
+    def get_factors(self, dtype="float64", device=False):
+        torch = _torch()
+        if device:
+            tdt = torch.float64 if dtype == "float64" else torch.float32
+            U = torch.empty((self.n_u, self.n_f), dtype=tdt, device="cuda")
+            M = torch.empty((self.n_m, self.n_f), dtype=tdt, device="cuda")
+            dt = ALS_DT_F64 if dtype == "float64" else ALS_DT_F32
+            _lib.check(self.lib.als_get_factors(self.ctx, U.data_ptr(), M.data_ptr(), dt, 1), "als_get_factors")
+            self.sync()
+            return U, M
+        npdt = np.float64 if dtype == "float64" else np.float32
+        U = np.empty((self.n_u, self.n_f), npdt)
+        M = np.empty((self.n_m, self.n_f), npdt)
+        dt = ALS_DT_F64 if dtype == "float64" else ALS_DT_F32
+        _lib.check(self.lib.als_get_factors(self.ctx, U.ctypes.data, M.ctypes.data, dt, 0), "als_get_factors")
+        return U, M
+
+    def get_x(self):
+        U, M = self.get_factors()
+        return np.concatenate([U.reshape(-1), M.reshape(-1)])
+
+    # -- algorithms -------------------------------------------------------------
+    def sweep(self, n=1):
+        _lib.check(self.lib.als_sweep(self.ctx, int(n)), "als_sweep")
+
+    def step(self, info=True):
+        if not info:
+            _lib.check(self.lib.alsncg_step(self.ctx, None), "alsncg_step")
+            return None
+        it = IterInfo()
+        _lib.check(self.lib.alsncg_step(self.ctx, ctypes.byref(it)), "alsncg_step")
+        return info_dict(it)
+
+    def run(self, max_iter, rel_tol=0.0, check_every=10):
+        it = IterInfo()
+        done = ctypes.c_int32(0)
+        _lib.check(self.lib.alsncg_run(self.ctx, int(max_iter), float(rel_tol), int(check_every),
+                                       ctypes.byref(it), ctypes.byref(done)), "alsncg_run")
+        d = info_dict(it)
+        d["iters"] = done.value
+        return d
+
+    def loss(self):
+        f = ctypes.c_double()
+        _lib.check(self.lib.als_loss(self.ctx, ctypes.byref(f)), "als_loss")
+        return f.value
+
+    def grad(self, want_vector=True):
+        gn = ctypes.c_double()
+        if want_vector:
+            g = np.empty((self.n_u + self.n_m) * self.n_f, np.float64)
+            _lib.check(self.lib.als_grad(self.ctx, g.ctypes.data, ALS_DT_F64, 0, ctypes.byref(gn)), "als_grad")
+            return g, gn.value
+        _lib.check(self.lib.als_grad(self.ctx, None, ALS_DT_F64, 0, ctypes.byref(gn)), "als_grad")
+        return None, gn.value
+
+    def linesearch_coeffs(self, p=None):
+        c = (ctypes.c_double * 5)()
+        if p is None:
+            _lib.check(self.lib.als_linesearch_coeffs(self.ctx, None, ALS_DT_F64, 0, c), "als_linesearch_coeffs")
+        else:
+            pb = _Buf(p, np.float64)
+            _lib.check(self.lib.als_linesearch_coeffs(self.ctx, pb.ptr, ALS_DT_F64, pb.on_device, c),
+                       "als_linesearch_coeffs")
+        return np.array(list(c))
+
+    def foldin(self, req_ptr, items, vals, dtype="float64"):
+        n_req = len(req_ptr) - 1
+        pb, ib, vb = _Buf(req_ptr, np.int64), _Buf(items, np.int32), _Buf(vals, np.float32)
+        npdt = np.float64 if dtype == "float64" else np.float32
+        out = np.empty((n_req, self.n_f), npdt)
+        dt = ALS_DT_F64 if dtype == "float64" else ALS_DT_F32
+        _lib.check(self.lib.als_foldin(self.ctx, n_req, pb.ptr, ib.ptr, vb.ptr, pb.on_device,
+                                       out.ctypes.data, dt, 0), "als_foldin")
+        return out
+
+    def sync(self):
+        _lib.check(self.lib.als_sync(self.ctx), "als_sync")

@@ -1,0 +1,99 @@
+"""ctypes declarations of the C ABI in include/als.h (argument marshalling only).
+
+Loading fails loudly if the CUDA library has not been built: there is no CPU
+fallback for any entry point.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libals.so")
+
+ALS_OK, ALS_EINVAL, ALS_ENOMEM, ALS_EBUDGET, ALS_ECUDA, ALS_ENOTSPD, ALS_ELINESEARCH, \
+    ALS_ETIMEOUT, ALS_EBUSY, ALS_ENOTSUP = range(10)
+STATUS_NAMES = {0: "ALS_OK", 1: "ALS_EINVAL", 2: "ALS_ENOMEM", 3: "ALS_EBUDGET", 4: "ALS_ECUDA",
+                5: "ALS_ENOTSPD", 6: "ALS_ELINESEARCH", 7: "ALS_ETIMEOUT", 8: "ALS_EBUSY",
+                9: "ALS_ENOTSUP"}
+ALS_FP64, ALS_MIXED = 0, 1
+ALS_LS_BACKTRACK, ALS_LS_EXACT = 0, 1
+ALS_DT_F64, ALS_DT_F32 = 0, 1
+ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC = 0, 1, 2
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n_f", ctypes.c_int32), ("lam", ctypes.c_double), ("precision", ctypes.c_int32),
+        ("ls_mode", ctypes.c_int32), ("ls_alpha0", ctypes.c_double), ("ls_tau", ctypes.c_double),
+        ("ls_c", ctypes.c_double), ("ls_max_shrinks", ctypes.c_int32),
+        ("refine_steps", ctypes.c_int32), ("gram_path", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_size_t), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class IterInfo(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int64), ("f", ctypes.c_double), ("gnorm", ctypes.c_double),
+        ("gnorm0", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+        ("c", ctypes.c_double * 5), ("shrinks", ctypes.c_int32), ("fallback", ctypes.c_int32),
+        ("fallbacks", ctypes.c_int64), ("notspd", ctypes.c_int64),
+    ]
+
+
+# name -> (restype, argtypes); the full list of symbols include/als.h declares
+_vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "als_config_default": (None, [ctypes.POINTER(Config)]),
+    "als_create": (_i32, [ctypes.POINTER(Config), _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i32, _vp,
+                          ctypes.POINTER(_vp)]),
+    "als_get_ratings": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "als_set_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "als_get_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "als_sweep": (_i32, [_vp, _i32]),
+    "alsncg_step": (_i32, [_vp, ctypes.POINTER(IterInfo)]),
+    "alsncg_run": (_i32, [_vp, _i32, _dbl, _i32, ctypes.POINTER(IterInfo), ctypes.POINTER(_i32)]),
+    "als_loss": (_i32, [_vp, ctypes.POINTER(_dbl)]),
+    "als_grad": (_i32, [_vp, _vp, _i32, _i32, ctypes.POINTER(_dbl)]),
+    "als_linesearch_coeffs": (_i32, [_vp, _vp, _i32, _i32, ctypes.POINTER(_dbl)]),
+    "als_foldin": (_i32, [_vp, _i64, _vp, _vp, _vp, _i32, _vp, _i32, _i32]),
+    "als_sync": (_i32, [_vp]),
+    "als_destroy": (None, [_vp]),
+    "als_last_error": (ctypes.c_char_p, []),
+    "als_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libals.so and declare every entry point.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"the CUDA library {path} is not built; run `python -c \"import __graft_entry__ as g; "
+            f"g.build()\"` (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class ALSError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.als_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, where):
+    if status != ALS_OK:
+        raise ALSError(status, where)

@@ -1,0 +1,686 @@
+// C ABI (include/als.h) and the host drivers of Algorithm 1 (ALS) and
+// Algorithm 2 (ALS-NCG).  The host only enqueues kernels: every arithmetic
+// step runs on the device, and the scalar decisions of Algorithm 2/3
+// (alpha, beta-bar, the fallback) are taken by device code, so an iteration
+// needs no host round trip and can be replayed as a CUDA graph.
+//
+// One Algorithm 2 iteration, k -> k+1 (x, p, g_k, gbar_k, s_k = gbar_k.g_k on
+// the device):
+//   1. Q coefficients c0..c4 at (x_k, p_k), one by-user pass (§V-C);
+//   2. Algorithm 3 on Q -> alpha_k (or the ALS-point fallback);
+//   3. x_{k+1} = x_k + alpha_k p_k;
+//   4. xbar = P(x_{k+1}) (U half, then M half), gbar_{k+1} = x_{k+1} - xbar;
+//   5. g_{k+1} = grad f(x_{k+1}) with gbar.g and gbar.(g_{k+1} - g_k) fused;
+//   6. beta-bar (Eq. 8), p_{k+1} = -gbar_{k+1} + beta-bar p_k.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.cuh"
+
+static thread_local std::string g_err;
+
+void als_set_error(const std::string &msg) { g_err = msg; }
+
+extern "C" const char *als_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *als_version(void) { return "als-ncg-gb300 1.0 (sm_103a)"; }
+
+als_status ctx_alloc(als_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (c->cfg.hbm_budget_bytes && c->allocated + bytes > c->cfg.hbm_budget_bytes) {
+        als_set_error("allocation of " + std::to_string(bytes) + " bytes exceeds hbm_budget_bytes");
+        return ALS_EBUDGET;
+    }
+    if (c->cfg.alloc) {
+        *p = c->cfg.alloc(bytes, (void *)c->stream, c->cfg.alloc_user);
+        if (!*p) {
+            als_set_error("allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+            return ALS_ENOMEM;
+        }
+    } else {
+        const cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            als_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return ALS_ENOMEM;
+        }
+    }
+    c->allocs.push_back({*p, bytes});
+    c->allocated += bytes;
+    return ALS_OK;
+}
+
+void ctx_free(als_ctx *c, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i) {
+        if (c->allocs[i].p == p) {
+            const size_t bytes = c->allocs[i].bytes;
+            if (c->cfg.free) c->cfg.free(p, bytes, (void *)c->stream, c->cfg.alloc_user);
+            else cudaFree(p);
+            c->allocated -= bytes;
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+namespace {
+
+bool valid_dtype(int d) { return d == ALS_DT_F64 || d == ALS_DT_F32; }
+size_t dtype_size(int d) { return d == ALS_DT_F64 ? 8 : 4; }
+
+LsParams ls_params(const als_ctx *c) {
+    LsParams p;
+    p.alpha0 = c->cfg.ls_alpha0;
+    p.tau = c->cfg.ls_tau;
+    p.c = c->cfg.ls_c;
+    p.max_shrinks = c->cfg.ls_max_shrinks;
+    p.mode = c->cfg.ls_mode;
+    return p;
+}
+
+char *vrow(const als_ctx *c, void *v, int64_t row) { return (char *)v + (size_t)row * c->ld * c->esz; }
+void *ublk(const als_ctx *c, void *v) { return v; }
+void *mblk(const als_ctx *c, void *v) { return vrow(c, v, c->n_u); }
+
+// One half of P(x): side 0 solves users from the M rows in F_M, side 1 items
+// from the U rows in F_U.
+als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void *Xout, void *Gbar) {
+    SweepArgs a;
+    a.ptr = side ? c->mptr : c->uptr;
+    a.idx = side ? c->midx : c->uidx;
+    a.val = side ? c->mval : c->uval;
+    a.order = side ? c->morder : c->uorder;
+    a.nrows = side ? c->n_m : c->n_u;
+    a.F = F;
+    a.Fbf = c->shadow;
+    a.Xin = Xin;
+    a.Xout = Xout;
+    a.Gbar = Gbar;
+    a.nf = c->nf;
+    a.ld = c->ld;
+    a.lambda = c->cfg.lambda;
+    a.refine = c->cfg.refine_steps;
+    a.notspd = c->dflags;
+    if (c->use_tc) {
+        als_status s = launch_to_bf16(c, F, side ? c->n_u : c->n_m, c->f64);
+        if (s != ALS_OK) return s;
+    }
+    return launch_sweep(c, a, c->f64, c->use_tc);
+}
+
+// xbar = P(x) with gbar = x - xbar, or in place (x <- P(x)) when Xout == X.
+als_status sweep_into(als_ctx *c, void *X, void *Xout, void *Gbar) {
+    als_status s = half_sweep(c, 0, mblk(c, X), ublk(c, X), ublk(c, Xout), Gbar ? ublk(c, Gbar) : nullptr);
+    if (s != ALS_OK) return s;
+    return half_sweep(c, 1, ublk(c, Xout), mblk(c, X), mblk(c, Xout), Gbar ? mblk(c, Gbar) : nullptr);
+}
+
+PassArgs pass_args(const als_ctx *c, int side) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.ptr = side ? c->mptr : c->uptr;
+    a.idx = side ? c->midx : c->uidx;
+    a.val = side ? c->mval : c->uval;
+    a.order = side ? c->morder : c->uorder;
+    a.nf = c->nf;
+    a.ld = c->ld;
+    a.lambda = c->cfg.lambda;
+    a.rowterm = c->rowterm;
+    a.stride = c->n_u + c->n_m;
+    a.rowoff = side ? c->n_u : 0;
+    return a;
+}
+
+// gradient of Eq. (1) at X into Gout; per-row terms |g|^2, gbar.g, gbar.(g-gprev)
+als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev) {
+    for (int side = 0; side < 2; ++side) {
+        PassArgs a = pass_args(c, side);
+        a.Xs = side ? mblk(c, X) : ublk(c, X);
+        a.Xo = side ? ublk(c, X) : mblk(c, X);
+        a.Gout = side ? mblk(c, Gout) : ublk(c, Gout);
+        a.Gbar = Gbar ? (side ? mblk(c, Gbar) : ublk(c, Gbar)) : nullptr;
+        a.Gprev = Gprev ? (side ? mblk(c, Gprev) : ublk(c, Gprev)) : nullptr;
+        const int64_t n = side ? c->n_m : c->n_u;
+        const int64_t nh = side ? c->nheavy_m : c->nheavy_u;
+        a.row_begin = 0;
+        a.nrows = nh;
+        als_status s = launch_grad(c, a, true);
+        if (s != ALS_OK) return s;
+        a.row_begin = nh;
+        a.nrows = n - nh;
+        s = launch_grad(c, a, false);
+        if (s != ALS_OK) return s;
+    }
+    return ALS_OK;
+}
+
+// Q coefficients at (X, P) (P == nullptr: only c0 = f(X)) into rowterm
+als_status lscoef_into(als_ctx *c, void *X, void *P) {
+    PassArgs a = pass_args(c, 0);
+    a.Xs = ublk(c, X);
+    a.Xo = mblk(c, X);
+    a.Ps = P ? ublk(c, P) : nullptr;
+    a.Po = P ? mblk(c, P) : nullptr;
+    a.row_begin = 0;
+    a.nrows = c->nheavy_u;
+    als_status s = launch_lscoef(c, a, true);
+    if (s != ALS_OK) return s;
+    a.row_begin = c->nheavy_u;
+    a.nrows = c->n_u - c->nheavy_u;
+    s = launch_lscoef(c, a, false);
+    if (s != ALS_OK) return s;
+    PassArgs b = pass_args(c, 1);
+    b.Xs = mblk(c, X);
+    b.Ps = P ? mblk(c, P) : nullptr;
+    b.row_begin = 0;
+    b.nrows = c->n_m;
+    return launch_lscoef_reg(c, b);
+}
+
+als_status read_scalars(als_ctx *c) {
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->hS, c->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ALS_OK;
+}
+
+als_status ncg_init(als_ctx *c) {
+    // gbar_0 = x_0 - P(x_0), g_0 = grad f(x_0), p_0 = -gbar_0, s_0 = gbar_0 . g_0
+    als_status s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+    if (s != ALS_OK) return s;
+    s = grad_into(c, c->X, c->G[c->gcur], c->Gbar, nullptr);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 3, c->n_u + c->n_m, S_RED, POST_INIT, ls_params(c));
+    if (s != ALS_OK) return s;
+    s = launch_neg_copy(c, c->P, c->Gbar, (size_t)(c->n_u + c->n_m) * c->ld);
+    if (s != ALS_OK) return s;
+    c->ncg_ready = true;
+    c->k = 0;
+    return ALS_OK;
+}
+
+// enqueue one Algorithm 2 iteration (graph-capturable: no host sync)
+als_status ncg_iter(als_ctx *c, int gcur) {
+    als_status s = lscoef_into(c, c->X, c->P);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 5, c->n_u + c->n_m, S_C, POST_LSELECT, ls_params(c));
+    if (s != ALS_OK) return s;
+    s = launch_update_x(c);
+    if (s != ALS_OK) return s;
+    s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+    if (s != ALS_OK) return s;
+    s = grad_into(c, c->X, c->G[gcur ^ 1], c->Gbar, c->G[gcur]);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 3, c->n_u + c->n_m, S_RED, POST_BETA, ls_params(c));
+    if (s != ALS_OK) return s;
+    return launch_update_p(c);
+}
+
+void fill_info(const als_ctx *c, als_iter_info *o) {
+    const double *S = c->hS;
+    o->k = c->k;
+    o->f = S[S_F];
+    o->gnorm = std::sqrt(S[S_GG]);
+    o->gnorm0 = std::sqrt(S[S_GG0]);
+    o->alpha = S[S_ALPHA];
+    o->beta = S[S_BETA];
+    for (int i = 0; i < 5; ++i) o->c[i] = S[S_C + i];
+    o->shrinks = (int32_t)S[S_SHRINK];
+    o->fallback = S[S_MODE] != 0.0;
+    o->fallbacks = (int64_t)S[S_NFALL];
+    o->notspd = c->hflags[0];
+}
+
+als_status loss_now(als_ctx *c, double *f) {
+    als_status s = lscoef_into(c, c->X, nullptr);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 1, c->n_u + c->n_m, S_RED, POST_NONE, ls_params(c));
+    if (s != ALS_OK) return s;
+    s = read_scalars(c);
+    if (s != ALS_OK) return s;
+    *f = c->hS[S_RED];
+    return ALS_OK;
+}
+
+void destroy_graphs(als_ctx *c) {
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+        c->graph[i] = nullptr;
+    }
+}
+
+als_status capture_graphs(als_ctx *c) {
+    for (int p = 0; p < 2; ++p) {
+        if (c->graph[p]) continue;
+        cudaGraph_t g = nullptr;
+        ALS_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        als_status s = ncg_iter(c, p);
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s != ALS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) {
+            als_set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+            return ALS_ECUDA;
+        }
+        const cudaError_t e2 = cudaGraphInstantiate(&c->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+            c->graph[p] = nullptr;
+            als_set_error(std::string("graph instantiate: ") + cudaGetErrorString(e2));
+            return ALS_ECUDA;
+        }
+    }
+    return ALS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" void als_config_default(als_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->n_f = 10;
+    cfg->lambda = 0.05;
+    cfg->precision = ALS_FP64;
+    cfg->ls_mode = ALS_LS_BACKTRACK;
+    cfg->ls_alpha0 = 10.0;
+    cfg->ls_tau = 0.9;
+    cfg->ls_c = 0.5;
+    cfg->ls_max_shrinks = 200;
+    cfg->refine_steps = 1;
+    cfg->gram_path = ALS_GRAM_AUTO;
+}
+
+extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
+                                 const int32_t *rows_or_null, const int64_t *rowptr_or_null,
+                                 const int32_t *cols, const float *vals, int on_device, void *cuda_stream,
+                                 als_ctx **out) {
+    if (!out) { als_set_error("als_create: out is NULL"); return ALS_EINVAL; }
+    *out = nullptr;
+    if (!cfg) { als_set_error("als_create: cfg is NULL"); return ALS_EINVAL; }
+    if (cfg->n_f < 1 || cfg->n_f > ALS_MAX_NF) { als_set_error("als_create: n_f must be in 1..128"); return ALS_EINVAL; }
+    if (!(cfg->lambda >= 0.0) || !std::isfinite(cfg->lambda)) { als_set_error("als_create: lambda must be finite and >= 0"); return ALS_EINVAL; }
+    if (cfg->precision != ALS_FP64 && cfg->precision != ALS_MIXED) { als_set_error("als_create: bad precision"); return ALS_EINVAL; }
+    if (cfg->ls_mode != ALS_LS_BACKTRACK && cfg->ls_mode != ALS_LS_EXACT) { als_set_error("als_create: bad ls_mode"); return ALS_EINVAL; }
+    if (!(cfg->ls_alpha0 > 0) || !(cfg->ls_tau > 0 && cfg->ls_tau < 1) || !(cfg->ls_c > 0 && cfg->ls_c < 1) || cfg->ls_max_shrinks < 0) {
+        als_set_error("als_create: line-search parameters need alpha0 > 0, 0 < tau < 1, 0 < c < 1");
+        return ALS_EINVAL;
+    }
+    if (cfg->refine_steps < 1 || cfg->refine_steps > 8) { als_set_error("als_create: refine_steps must be 1..8"); return ALS_EINVAL; }
+    if (n_u < 1 || n_m < 1 || n_u >= (1ll << 31) || n_m >= (1ll << 31) || nnz < 0 || nnz >= (1ll << 40)) {
+        als_set_error("als_create: need 1 <= n_u, n_m < 2^31 and 0 <= nnz < 2^40");
+        return ALS_EINVAL;
+    }
+    if (nnz > 0 && (!cols || !vals || (!rows_or_null && !rowptr_or_null))) {
+        als_set_error("als_create: ratings arrays are NULL");
+        return ALS_EINVAL;
+    }
+    if (rowptr_or_null == nullptr && nnz > 0 && rows_or_null == nullptr) { als_set_error("als_create: rows is NULL"); return ALS_EINVAL; }
+    if (nnz >= (1ll << 32)) { als_set_error("als_create: nnz >= 2^32 is not supported by the builder"); return ALS_ENOTSUP; }
+
+    als_ctx *c = new als_ctx();
+    c->cfg = *cfg;
+    c->n_u = n_u; c->n_m = n_m; c->nnz = nnz;
+    c->nf = cfg->n_f;
+    c->ld = (cfg->n_f + 3) & ~3;
+    c->f64 = cfg->precision == ALS_FP64;
+    c->esz = c->f64 ? 8 : 4;
+    auto fail = [&](als_status s) { als_destroy(c); return s; };
+    if (cudaGetDevice(&c->dev) != cudaSuccess) { cudaGetLastError(); als_set_error("als_create: no CUDA device"); return fail(ALS_ECUDA); }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) { cudaGetLastError(); als_set_error("als_create: cudaGetDeviceProperties failed"); return fail(ALS_ECUDA); }
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        char b[160];
+        snprintf(b, sizeof b, "als_create: this library is built for sm_103a (GB300); device is sm_%d%d", prop.major, prop.minor);
+        als_set_error(b);
+        return fail(ALS_ENOTSUP);
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (!c->stream) {
+        // the legacy default stream cannot be captured into a graph: own a stream
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            als_set_error("als_create: cudaStreamCreateWithFlags failed");
+            return fail(ALS_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    c->use_tc = false;
+    if (cfg->gram_path == ALS_GRAM_TC && c->f64) { als_set_error("als_create: the tensor-core Gram needs ALS_MIXED"); return fail(ALS_EINVAL); }
+    if (cfg->gram_path == ALS_GRAM_TC) c->use_tc = true;
+
+    const int64_t nrows = n_u + n_m;
+    const size_t vbytes = (size_t)nrows * c->ld * c->esz;
+    als_status s;
+#define ALLOC(ptr, bytes) do { void *_p = nullptr; s = ctx_alloc(c, &_p, (bytes)); if (s != ALS_OK) return fail(s); ptr = (decltype(ptr))_p; } while (0)
+    ALLOC(c->uptr, (n_u + 1) * sizeof(int64_t));
+    ALLOC(c->mptr, (n_m + 1) * sizeof(int64_t));
+    ALLOC(c->uidx, nnz * sizeof(int32_t));
+    ALLOC(c->midx, nnz * sizeof(int32_t));
+    ALLOC(c->uval, nnz * sizeof(float));
+    ALLOC(c->mval, nnz * sizeof(float));
+    ALLOC(c->uorder, n_u * sizeof(int32_t));
+    ALLOC(c->morder, n_m * sizeof(int32_t));
+    ALLOC(c->X, vbytes);
+    ALLOC(c->Xbar, vbytes);
+    ALLOC(c->Gbar, vbytes);
+    ALLOC(c->G[0], vbytes);
+    ALLOC(c->G[1], vbytes);
+    ALLOC(c->P, vbytes);
+    ALLOC(c->tmpvec, (size_t)nrows * c->ld * 8);
+    ALLOC(c->rowterm, 5 * (size_t)nrows * sizeof(double));
+    ALLOC(c->partial, 5 * RED_MAXB * sizeof(double));
+    ALLOC(c->ticket, 256);
+    ALLOC(c->S, S_COUNT * sizeof(double));
+    ALLOC(c->dflags, 16 * sizeof(int));
+    if (c->use_tc) {
+        c->shadow_rows = std::max(n_u, n_m);
+        ALLOC(c->shadow, (size_t)c->shadow_rows * ALS_TC_LD * sizeof(__nv_bfloat16));
+    }
+#undef ALLOC
+    if (cudaMallocHost(&c->hS, S_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->hflags, 16 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        als_set_error("als_create: pinned host allocation failed");
+        return fail(ALS_ENOMEM);
+    }
+    for (void *p : {c->X, c->Xbar, c->Gbar, c->G[0], c->G[1], c->P}) {
+        if (cudaMemsetAsync(p, 0, vbytes, c->stream) != cudaSuccess) { cudaGetLastError(); als_set_error("als_create: memset failed"); return fail(ALS_ECUDA); }
+    }
+    if (cudaMemsetAsync(c->ticket, 0, 256, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->S, 0, S_COUNT * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->rowterm, 0, 5 * (size_t)nrows * sizeof(double), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        als_set_error("als_create: memset failed");
+        return fail(ALS_ECUDA);
+    }
+    s = build_ratings(c, rows_or_null, rowptr_or_null, cols, vals, on_device);
+    if (s != ALS_OK) return fail(s);
+    if (cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return fail(ALS_ECUDA); }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        als_set_error(std::string("als_create: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(ALS_ECUDA);
+    }
+    *out = c;
+    return ALS_OK;
+}
+
+extern "C" als_status als_get_ratings(als_ctx *c, int64_t *uptr, int32_t *uidx, float *uval, int64_t *mptr,
+                                      int32_t *midx, float *mval, int32_t *uorder, int32_t *morder) {
+    if (!c) { als_set_error("als_get_ratings: ctx is NULL"); return ALS_EINVAL; }
+    const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    if (uptr) ALS_CUDA_TRY(cudaMemcpyAsync(uptr, c->uptr, (c->n_u + 1) * sizeof(int64_t), k, c->stream));
+    if (mptr) ALS_CUDA_TRY(cudaMemcpyAsync(mptr, c->mptr, (c->n_m + 1) * sizeof(int64_t), k, c->stream));
+    if (c->nnz > 0) {
+        if (uidx) ALS_CUDA_TRY(cudaMemcpyAsync(uidx, c->uidx, c->nnz * sizeof(int32_t), k, c->stream));
+        if (uval) ALS_CUDA_TRY(cudaMemcpyAsync(uval, c->uval, c->nnz * sizeof(float), k, c->stream));
+        if (midx) ALS_CUDA_TRY(cudaMemcpyAsync(midx, c->midx, c->nnz * sizeof(int32_t), k, c->stream));
+        if (mval) ALS_CUDA_TRY(cudaMemcpyAsync(mval, c->mval, c->nnz * sizeof(float), k, c->stream));
+    }
+    if (uorder) ALS_CUDA_TRY(cudaMemcpyAsync(uorder, c->uorder, c->n_u * sizeof(int32_t), k, c->stream));
+    if (morder) ALS_CUDA_TRY(cudaMemcpyAsync(morder, c->morder, c->n_m * sizeof(int32_t), k, c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ALS_OK;
+}
+
+extern "C" als_status als_set_factors(als_ctx *c, const void *U, const void *M, int dtype, int on_device) {
+    if (!c || !U || !M || !valid_dtype(dtype)) { als_set_error("als_set_factors: bad argument"); return ALS_EINVAL; }
+    const size_t es = dtype_size(dtype);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->tmpvec, U, (size_t)c->n_u * c->nf * es, kind, c->stream));
+    als_status s = launch_convert_in(c, c->X, c->tmpvec, c->n_u, dtype, c->nf);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->tmpvec, M, (size_t)c->n_m * c->nf * es, kind, c->stream));
+    s = launch_convert_in(c, mblk(c, c->X), c->tmpvec, c->n_m, dtype, c->nf);
+    if (s != ALS_OK) return s;
+    if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->ncg_ready = false;
+    c->k = 0;
+    return ALS_OK;
+}
+
+extern "C" als_status als_get_factors(als_ctx *c, void *U, void *M, int dtype, int on_device) {
+    if (!c || !U || !M || !valid_dtype(dtype)) { als_set_error("als_get_factors: bad argument"); return ALS_EINVAL; }
+    const size_t es = dtype_size(dtype);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    als_status s = launch_convert_out(c, c->tmpvec, c->X, c->n_u, dtype, c->nf);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaMemcpyAsync(U, c->tmpvec, (size_t)c->n_u * c->nf * es, kind, c->stream));
+    if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    s = launch_convert_out(c, c->tmpvec, mblk(c, c->X), c->n_m, dtype, c->nf);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaMemcpyAsync(M, c->tmpvec, (size_t)c->n_m * c->nf * es, kind, c->stream));
+    if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ALS_OK;
+}
+
+extern "C" als_status als_sweep(als_ctx *c, int32_t n_sweeps) {
+    if (!c || n_sweeps < 0) { als_set_error("als_sweep: bad argument"); return ALS_EINVAL; }
+    for (int i = 0; i < n_sweeps; ++i) {
+        als_status s = sweep_into(c, c->X, c->X, nullptr);
+        if (s != ALS_OK) return s;
+    }
+    c->ncg_ready = false;
+    return ALS_OK;
+}
+
+extern "C" als_status alsncg_step(als_ctx *c, als_iter_info *out) {
+    if (!c) { als_set_error("alsncg_step: ctx is NULL"); return ALS_EINVAL; }
+    als_status s;
+    if (!c->ncg_ready) {
+        s = ncg_init(c);
+        if (s != ALS_OK) return s;
+    }
+    s = ncg_iter(c, c->gcur);
+    if (s != ALS_OK) return s;
+    c->gcur ^= 1;
+    c->k += 1;
+    if (out) {
+        s = read_scalars(c);
+        if (s != ALS_OK) return s;
+        fill_info(c, out);
+        if (out->fallback) {
+            double f;
+            s = loss_now(c, &f);
+            if (s != ALS_OK) return s;
+            out->f = f;
+        }
+    }
+    return ALS_OK;
+}
+
+extern "C" als_status alsncg_run(als_ctx *c, int32_t max_iter, double rel_tol, int32_t check_every,
+                                 als_iter_info *last, int32_t *iters_done) {
+    if (!c || max_iter < 0 || check_every < 1) { als_set_error("alsncg_run: bad argument"); return ALS_EINVAL; }
+    als_status s;
+    if (!c->ncg_ready) {
+        s = ncg_init(c);
+        if (s != ALS_OK) return s;
+    }
+    s = capture_graphs(c);
+    if (s != ALS_OK) return s;
+    int32_t done = 0;
+    bool converged = false;
+    while (done < max_iter && !converged) {
+        ALS_CUDA_TRY(cudaGraphLaunch(c->graph[c->gcur], c->stream));
+        c->gcur ^= 1;
+        c->k += 1;
+        ++done;
+        if (done % check_every == 0 || done == max_iter) {
+            s = read_scalars(c);
+            if (s != ALS_OK) return s;
+            converged = std::sqrt(c->hS[S_GG]) <= rel_tol * std::sqrt(c->hS[S_GG0]);
+        }
+    }
+    if (iters_done) *iters_done = done;
+    if (last) {
+        s = read_scalars(c);
+        if (s != ALS_OK) return s;
+        fill_info(c, last);
+    }
+    return ALS_OK;
+}
+
+extern "C" als_status als_loss(als_ctx *c, double *f) {
+    if (!c || !f) { als_set_error("als_loss: bad argument"); return ALS_EINVAL; }
+    return loss_now(c, f);
+}
+
+extern "C" als_status als_grad(als_ctx *c, void *g_out, int dtype, int on_device, double *gnorm) {
+    if (!c || (g_out && !valid_dtype(dtype))) { als_set_error("als_grad: bad argument"); return ALS_EINVAL; }
+    // G[gcur ^ 1] is free between ALS-NCG iterations (the next one overwrites it)
+    void *G = c->G[c->gcur ^ 1];
+    als_status s = grad_into(c, c->X, G, nullptr, nullptr);
+    if (s != ALS_OK) return s;
+    if (gnorm) {
+        s = launch_reduce(c, 1, c->n_u + c->n_m, S_RED, POST_NONE, ls_params(c));
+        if (s != ALS_OK) return s;
+    }
+    if (g_out) {
+        const size_t es = dtype_size(dtype);
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        s = launch_convert_out(c, c->tmpvec, G, c->n_u + c->n_m, dtype, c->nf);
+        if (s != ALS_OK) return s;
+        ALS_CUDA_TRY(cudaMemcpyAsync(g_out, c->tmpvec, (size_t)(c->n_u + c->n_m) * c->nf * es, kind, c->stream));
+    }
+    if (gnorm) {
+        s = read_scalars(c);
+        if (s != ALS_OK) return s;
+        *gnorm = std::sqrt(c->hS[S_RED]);
+    } else if (g_out && !on_device) {
+        ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return ALS_OK;
+}
+
+extern "C" als_status als_linesearch_coeffs(als_ctx *c, const void *p, int dtype, int on_device, double cf[5]) {
+    if (!c || !cf || (p && !valid_dtype(dtype))) { als_set_error("als_linesearch_coeffs: bad argument"); return ALS_EINVAL; }
+    void *P = c->P;
+    if (p) {
+        // stage the caller's direction in G[gcur^1] (unused between iterations)
+        void *dst = c->G[c->gcur ^ 1];
+        const size_t es = dtype_size(dtype);
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        ALS_CUDA_TRY(cudaMemcpyAsync(c->tmpvec, p, (size_t)(c->n_u + c->n_m) * c->nf * es, kind, c->stream));
+        als_status s = launch_convert_in(c, dst, c->tmpvec, c->n_u + c->n_m, dtype, c->nf);
+        if (s != ALS_OK) return s;
+        P = dst;
+    } else if (!c->ncg_ready) {
+        als_set_error("als_linesearch_coeffs: no direction given and ALS-NCG has not started");
+        return ALS_EINVAL;
+    }
+    als_status s = lscoef_into(c, c->X, P);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 5, c->n_u + c->n_m, S_RED, POST_NONE, ls_params(c));
+    if (s != ALS_OK) return s;
+    s = read_scalars(c);
+    if (s != ALS_OK) return s;
+    for (int i = 0; i < 5; ++i) cf[i] = c->hS[S_RED + i];
+    return ALS_OK;
+}
+
+extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_ptr, const int32_t *items,
+                                 const float *vals, int on_device_in, void *u_out, int dtype, int on_device_out) {
+    if (!c || n_req < 0 || (n_req > 0 && (!req_ptr || !u_out)) || !valid_dtype(dtype)) {
+        als_set_error("als_foldin: bad argument");
+        return ALS_EINVAL;
+    }
+    if (n_req == 0) return ALS_OK;
+    int64_t total = 0;
+    const cudaMemcpyKind kin = on_device_in ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    ALS_CUDA_TRY(cudaMemcpyAsync(&total, req_ptr + n_req, sizeof(int64_t), kin, c->stream));
+    int64_t first = 0;
+    ALS_CUDA_TRY(cudaMemcpyAsync(&first, req_ptr, sizeof(int64_t), kin, c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (first != 0 || total < 0 || (total > 0 && (!items || !vals))) {
+        als_set_error("als_foldin: req_ptr[0] must be 0 and req_ptr[n_req] >= 0");
+        return ALS_EINVAL;
+    }
+    // device copies of the requests
+    int64_t *dptr = nullptr;
+    int32_t *didx = nullptr;
+    float *dval = nullptr;
+    void *dout = nullptr;
+    als_status s;
+    auto cleanup = [&]() { ctx_free(c, dptr); ctx_free(c, didx); ctx_free(c, dval); ctx_free(c, dout); };
+    if ((s = ctx_alloc(c, (void **)&dptr, (n_req + 1) * sizeof(int64_t))) != ALS_OK) { cleanup(); return s; }
+    if ((s = ctx_alloc(c, (void **)&didx, std::max<int64_t>(total, 1) * sizeof(int32_t))) != ALS_OK) { cleanup(); return s; }
+    if ((s = ctx_alloc(c, (void **)&dval, std::max<int64_t>(total, 1) * sizeof(float))) != ALS_OK) { cleanup(); return s; }
+    if ((s = ctx_alloc(c, (void **)&dout, (size_t)n_req * c->ld * 8)) != ALS_OK) { cleanup(); return s; }
+    const cudaMemcpyKind k2 = on_device_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+#define TRY(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { cleanup(); als_set_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); return ALS_ECUDA; } } while (0)
+    TRY(cudaMemcpyAsync(dptr, req_ptr, (n_req + 1) * sizeof(int64_t), k2, c->stream));
+    if (total > 0) {
+        TRY(cudaMemcpyAsync(didx, items, total * sizeof(int32_t), k2, c->stream));
+        TRY(cudaMemcpyAsync(dval, vals, total * sizeof(float), k2, c->stream));
+    }
+    // reject out-of-range item ids, non-finite values and a decreasing req_ptr
+    s = launch_check_requests(c, dptr, n_req, didx, dval, total, c->n_m, c->dflags + 6);
+    if (s != ALS_OK) { cleanup(); return s; }
+    TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    if (c->hflags[6]) {
+        cleanup();
+        als_set_error("als_foldin: item id out of range, non-finite rating or decreasing req_ptr");
+        return ALS_EINVAL;
+    }
+    SweepArgs a;
+    a.ptr = dptr;
+    a.idx = didx;
+    a.val = dval;
+    a.order = nullptr;
+    a.nrows = n_req;
+    a.F = mblk(c, c->X);
+    a.Fbf = c->shadow;
+    a.Xin = nullptr;
+    a.Xout = dout;
+    a.Gbar = nullptr;
+    a.nf = c->nf;
+    a.ld = c->ld;
+    a.lambda = c->cfg.lambda;
+    a.refine = c->cfg.refine_steps + 1;  // cold start: one more correction
+    a.notspd = c->dflags + 5;
+    if (c->use_tc) {
+        s = launch_to_bf16(c, a.F, c->n_m, c->f64);
+        if (s != ALS_OK) { cleanup(); return s; }
+    }
+    s = launch_sweep(c, a, c->f64, c->use_tc);
+    if (s != ALS_OK) { cleanup(); return s; }
+    s = launch_convert_out(c, c->tmpvec, dout, n_req, dtype, c->nf);
+    if (s != ALS_OK) { cleanup(); return s; }
+    const cudaMemcpyKind ko = on_device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TRY(cudaMemcpyAsync(u_out, c->tmpvec, (size_t)n_req * c->nf * dtype_size(dtype), ko, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+#undef TRY
+    cleanup();
+    return ALS_OK;
+}
+
+extern "C" als_status als_sync(als_ctx *c) {
+    if (!c) { als_set_error("als_sync: ctx is NULL"); return ALS_EINVAL; }
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return ALS_OK;
+}
+
+extern "C" void als_destroy(als_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    destroy_graphs(c);
+    while (!c->allocs.empty()) ctx_free(c, c->allocs.back().p);
+    if (c->hS) cudaFreeHost(c->hS);
+    if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}

@@ -1,0 +1,171 @@
+// Internal declarations of the ALS / ALS-NCG CUDA library (sm_103a).
+// The public boundary is include/als.h; everything here is private.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "als.h"
+
+#define ALS_MAX_NF 128
+#define ALS_TC_LD 128          // bf16 shadow row length used by the tcgen05 Gram
+#define ALS_HEAVY_MIN 2048     // rows at least this long get a whole CTA in the passes
+
+// Slots of the device scalar block (double S[]).
+enum {
+    S_C = 0,        // c0..c4 of Q(alpha), 5 slots
+    S_ALPHA = 5,    // accepted step
+    S_BETA = 6,     // beta-bar of Eq. (8)
+    S_S = 7,        // gbar_k . g_k
+    S_GG = 8,       // |g_k|^2
+    S_GBG = 9,      // gbar_{k+1} . g_{k+1}
+    S_GBD = 10,     // gbar_{k+1} . (g_{k+1} - g_k)
+    S_F = 11,       // f(x_k) from Q(alpha)
+    S_MODE = 12,    // 1: fallback step (ALS point), 0: line-search step
+    S_SHRINK = 13,  // backtracking count
+    S_NFALL = 14,   // total fallbacks
+    S_GG0 = 15,     // |g_0|^2
+    S_RED = 16,     // 5 slots: plain reduction results (loss, |g|^2, ...)
+    S_COUNT = 24
+};
+
+// Post-operations run by the last block of a reduction (one thread, FP64).
+enum { POST_NONE = 0, POST_LSELECT = 1, POST_BETA = 2, POST_INIT = 3 };
+
+struct LsParams {
+    double alpha0, tau, c;
+    int max_shrinks;
+    int mode;   // als_ls_mode
+};
+
+struct DevAlloc {
+    void *p;
+    size_t bytes;
+};
+
+struct als_ctx {
+    als_config cfg;
+    int64_t n_u = 0, n_m = 0, nnz = 0;
+    int nf = 0, ld = 0;
+    bool f64 = true;
+    int dev = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t allocated = 0;
+    std::vector<DevAlloc> allocs;
+
+    // ratings: by user (CSR) and by item (CSC); rows in degree-descending order
+    int64_t *uptr = nullptr, *mptr = nullptr;
+    int32_t *uidx = nullptr, *midx = nullptr;
+    float *uval = nullptr, *mval = nullptr;
+    int32_t *uorder = nullptr, *morder = nullptr;
+    int64_t nheavy_u = 0, nheavy_m = 0;
+    int64_t maxdeg_u = 0, maxdeg_m = 0;
+
+    // iterate and NCG vectors, (n_u + n_m) x ld each, element size esz
+    size_t esz = 8;
+    void *X = nullptr, *Xbar = nullptr, *Gbar = nullptr, *G[2] = {nullptr, nullptr}, *P = nullptr;
+    int gcur = 0;
+    void *tmpvec = nullptr;          // staging for user-supplied vectors
+    __nv_bfloat16 *shadow = nullptr; // bf16 copy of the fixed side (tcgen05 Gram)
+    int64_t shadow_rows = 0;
+
+    // deterministic reductions
+    double *rowterm = nullptr;   // 5 x (n_u + n_m)
+    double *partial = nullptr;   // 5 x RED_MAXB
+    unsigned *ticket = nullptr;
+    double *S = nullptr;         // S_COUNT scalars
+    int *dflags = nullptr;       // [0] rows not SPD, [1] validation errors, [2] duplicates
+    double *hS = nullptr;        // pinned host mirror of S
+    int *hflags = nullptr;
+
+    // Algorithm 2 state
+    bool ncg_ready = false;
+    int64_t k = 0;
+    bool use_tc = false;
+
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+#define RED_MAXB 512
+
+// ---------------------------------------------------------------------------
+// error reporting
+void als_set_error(const std::string &msg);
+#define ALS_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            als_set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));          \
+            return ALS_ECUDA;                                                           \
+        }                                                                               \
+    } while (0)
+
+// allocation through the configured hooks, counted against the HBM budget
+als_status ctx_alloc(als_ctx *c, void **p, size_t bytes);
+void ctx_free(als_ctx *c, void *p);
+
+// ---------------------------------------------------------------------------
+// builder (builder.cu)
+als_status build_ratings(als_ctx *c, const int32_t *rows, const int64_t *rowptr,
+                         const int32_t *cols, const float *vals, int on_device);
+
+// ---------------------------------------------------------------------------
+// sweep (sweep.cu): one half of Algorithm 1 over a list of rows
+struct SweepArgs {
+    const int64_t *ptr;     // row r's ratings: [ptr[r], ptr[r+1])
+    const int32_t *idx;     // fixed-side ids
+    const float *val;       // ratings
+    const int32_t *order;   // rows to process, in this order (nullptr = 0..nrows-1)
+    int64_t nrows;
+    const void *F;          // fixed-side factors, ld-strided (T)
+    const __nv_bfloat16 *Fbf;  // bf16 shadow of F (ALS_TC_LD-strided), tcgen05 path
+    const void *Xin;        // current rows (warm start; Gbar = Xin - Xout); may be null
+    void *Xout;             // solved rows
+    void *Gbar;             // optional Gbar rows
+    int nf, ld;
+    double lambda;
+    int refine;
+    int *notspd;
+};
+als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
+als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64);
+
+// ---------------------------------------------------------------------------
+// passes (passes.cu)
+struct PassArgs {
+    const int64_t *ptr;
+    const int32_t *idx;
+    const float *val;
+    const int32_t *order;
+    int64_t row_begin, nrows;   // positions [row_begin, row_begin + nrows) of order
+    const void *Xs;             // this side's rows (x)
+    const void *Ps;             // this side's direction rows (p), may be null
+    const void *Xo;             // other side's rows (x)
+    const void *Po;             // other side's direction rows (p), may be null
+    void *Gout;                 // gradient rows out
+    const void *Gbar;           // this side's gbar rows (may be null)
+    const void *Gprev;          // this side's previous gradient rows (may be null)
+    int nf, ld;
+    double lambda;
+    double *rowterm;            // rowterm[t * stride + rowoff + row]
+    int64_t stride, rowoff;
+};
+als_status launch_grad(als_ctx *c, const PassArgs &a, bool heavy);
+als_status launch_lscoef(als_ctx *c, const PassArgs &a, bool heavy);
+als_status launch_lscoef_reg(als_ctx *c, const PassArgs &a);  // rows without rating terms
+als_status launch_reduce(als_ctx *c, int nterms, int64_t n, int s_off, int post,
+                         const LsParams &lp);
+als_status launch_update_x(als_ctx *c);   // x <- x + alpha p, or x <- xbar on fallback
+als_status launch_update_p(als_ctx *c);   // p <- -gbar + beta p
+als_status launch_neg_copy(als_ctx *c, void *dst, const void *src, size_t n);  // dst = -src
+als_status launch_convert_in(als_ctx *c, void *dst, const void *src, int64_t rows, int src_dtype,
+                             int src_ld);
+als_status launch_convert_out(als_ctx *c, void *dst, const void *src, int64_t rows, int dst_dtype,
+                              int dst_ld);
+als_status launch_check_requests(als_ctx *c, const int64_t *ptr, int64_t nreq, const int32_t *idx,
+                                 const float *val, int64_t total, int64_t bound, int *flag);

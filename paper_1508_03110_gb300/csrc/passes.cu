@@ -1,0 +1,721 @@
+// Rating passes, deterministic reductions and NCG vector kernels.
+//
+//  * k_grad: gradient of Eq. (1) for one side (§V-C "Gradient Evaluation"):
+//      g_i = 2 lambda n_i x_i - 2 sum_{e in row i} (r_e - x_i . f_e) f_e,
+//    with the fixed side f, plus per-row FP64 terms |g_i|^2,
+//    gbar_i . g_i and gbar_i . (g_i - gprev_i) for Eq. (8).
+//  * k_lscoef: the five coefficients of Q(alpha) = f(x + alpha p) (§V-C
+//    "Line Search & Loss Function Evaluation"), one pass over the by-user
+//    ratings with four dot products per rating; with p = 0 it is the loss.
+//  * k_reduce: fixed-order two-level FP64 sums of the per-row terms, and the
+//    scalar step that follows them (Algorithm 3 on Q, beta-bar of Eq. 8).
+//  * vector kernels: x <- x + alpha p (or the ALS point on a fallback),
+//    p <- -gbar + beta p, conversions.
+//
+// Layout: a row of n_f values is stored in ld = round_up(n_f, 4) slots (the
+// padding is kept at zero).  A group of LPR lanes owns one row, each lane one
+// 4-wide slot, so a rating costs one 16 B (float) / 32 B (double) load per
+// lane and a log2(LPR)-step shuffle reduction for each dot product.  Rows of
+// at least ALS_HEAVY_MIN ratings are processed by a whole CTA (contiguous
+// segments per group, combined in a fixed order).  No floating-point atomics
+// anywhere: every per-row term lands in its own slot and is summed in a fixed
+// order, so results are bit-reproducible.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ void zero4(T (&v)[4]) { v[0] = v[1] = v[2] = v[3] = T(0); }
+
+template <typename T>
+__device__ __forceinline__ T dot4(const T (&a)[4], const T (&b)[4]) {
+    T s = a[0] * b[0];
+    s = fma(a[1], b[1], s);
+    s = fma(a[2], b[2], s);
+    s = fma(a[3], b[3], s);
+    return s;
+}
+
+template <int LPR, typename V>
+__device__ __forceinline__ V gsum(V x, unsigned mask) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+    return x;
+}
+
+template <int LPR>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    if (LPR == 32) return 0xffffffffu;
+    return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
+}
+
+// ---------------------------------------------------------------------------
+// gradient
+// ---------------------------------------------------------------------------
+template <typename T, int LPR>
+__device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
+                                            unsigned mask, const T (&x)[4], const T (&acc)[4]) {
+    const int nslot = a.ld / 4;
+    const bool act = gl < nslot;
+    const T l2 = (T)(2.0 * a.lambda * (double)n);
+    T g[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = l2 * x[i] - T(2) * acc[i];
+    double tg = 0, tgb = 0, tgd = 0;
+    if (act) {
+        st4(reinterpret_cast<T *>(a.Gout) + row * a.ld + 4 * gl, g);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tg += (double)g[i] * (double)g[i];
+        if (a.Gbar) {
+            T gb[4];
+            ld4(reinterpret_cast<const T *>(a.Gbar) + row * a.ld + 4 * gl, gb);
+            T gp[4];
+            if (a.Gprev) ld4(reinterpret_cast<const T *>(a.Gprev) + row * a.ld + 4 * gl, gp);
+            else zero4(gp);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                tgb += (double)gb[i] * (double)g[i];
+                tgd += (double)gb[i] * ((double)g[i] - (double)gp[i]);
+            }
+        }
+    }
+    tg = gsum<LPR>(tg, mask);
+    tgb = gsum<LPR>(tgb, mask);
+    tgd = gsum<LPR>(tgd, mask);
+    if (gl == 0) {
+        const int64_t o = a.rowoff + row;
+        a.rowterm[o] = tg;
+        a.rowterm[a.stride + o] = tgb;
+        a.rowterm[2 * a.stride + o] = tgd;
+    }
+}
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(256) k_grad(PassArgs a) {
+    const int lane = threadIdx.x & 31, gl = lane % LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const int nslot = a.ld / 4;
+    const bool act = gl < nslot;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / LPR;
+    const T *Xs = reinterpret_cast<const T *>(a.Xs);
+    const T *Xo = reinterpret_cast<const T *>(a.Xo);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR; r < a.nrows; r += ngroups) {
+        const int64_t row = a.order[a.row_begin + r];
+        const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
+        T x[4], acc[4];
+        zero4(acc);
+        if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
+        int64_t e = 0;
+        for (; e + 2 <= n; e += 2) {
+            const int64_t j0 = a.idx[beg + e], j1 = a.idx[beg + e + 1];
+            T f0[4], f1[4];
+            if (act) { ld4(Xo + j0 * a.ld + 4 * gl, f0); ld4(Xo + j1 * a.ld + 4 * gl, f1); }
+            else { zero4(f0); zero4(f1); }
+            T d0 = gsum<LPR>(dot4(x, f0), mask);
+            T d1 = gsum<LPR>(dot4(x, f1), mask);
+            const T e0 = (T)a.val[beg + e] - d0, e1 = (T)a.val[beg + e + 1] - d1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(e1, f1[i], fma(e0, f0[i], acc[i]));
+        }
+        for (; e < n; ++e) {
+            const int64_t j0 = a.idx[beg + e];
+            T f0[4];
+            if (act) ld4(Xo + j0 * a.ld + 4 * gl, f0); else zero4(f0);
+            const T d0 = gsum<LPR>(dot4(x, f0), mask);
+            const T e0 = (T)a.val[beg + e] - d0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(e0, f0[i], acc[i]);
+        }
+        grad_finish<T, LPR>(a, row, n, gl, mask, x, acc);
+    }
+}
+
+// one CTA (256 threads) per heavy row; groups take contiguous segments
+template <typename T, int LPR>
+__global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
+    constexpr int NG = 256 / LPR;
+    __shared__ T part[NG][LPR][4];
+    const int lane = threadIdx.x & 31, gl = lane % LPR, gi = threadIdx.x / LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const bool act = gl < a.ld / 4;
+    const T *Xs = reinterpret_cast<const T *>(a.Xs);
+    const T *Xo = reinterpret_cast<const T *>(a.Xo);
+    for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+        const int64_t row = a.order[a.row_begin + r];
+        const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
+        const int64_t seg = (n + NG - 1) / NG;
+        const int64_t e0 = beg + gi * seg, e1 = min(beg + n, e0 + seg);
+        T x[4], acc[4];
+        zero4(acc);
+        if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t j = a.idx[e];
+            T f[4];
+            if (act) ld4(Xo + j * a.ld + 4 * gl, f); else zero4(f);
+            const T d = gsum<LPR>(dot4(x, f), mask);
+            const T er = (T)a.val[e] - d;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(er, f[i], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) part[gi][gl][i] = acc[i];
+        __syncthreads();
+        if (gi == 0) {
+            T tot[4];
+            zero4(tot);
+            for (int q = 0; q < NG; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tot[i] += part[q][gl][i];
+            grad_finish<T, LPR>(a, row, n, gl, mask, x, tot);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// line-search coefficients (and the loss when Ps == Po == null)
+// ---------------------------------------------------------------------------
+template <typename T, int LPR, bool HAS_P>
+__device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4], const T *Xo,
+                                              const T *Po, int64_t j, float r, int ld, int gl,
+                                              bool act, unsigned mask, double (&t)[5]) {
+    T xm[4], pm[4];
+    if (act) {
+        ld4(Xo + j * ld + 4 * gl, xm);
+        if (HAS_P) ld4(Po + j * ld + 4 * gl, pm); else zero4(pm);
+    } else {
+        zero4(xm); zero4(pm);
+    }
+    const T d0 = gsum<LPR>(dot4(xu, xm), mask);
+    const double e0 = (double)r - (double)d0;
+    if (HAS_P) {
+        const T d1 = gsum<LPR>(dot4(xu, pm), mask);
+        const T d2 = gsum<LPR>(dot4(pu, xm), mask);
+        const T d3 = gsum<LPR>(dot4(pu, pm), mask);
+        const double aa = (double)d1 + (double)d2, b = (double)d3;
+        t[0] += e0 * e0;
+        t[1] += -2.0 * e0 * aa;
+        t[2] += aa * aa - 2.0 * e0 * b;
+        t[3] += 2.0 * aa * b;
+        t[4] += b * b;
+    } else {
+        t[0] += e0 * e0;
+    }
+}
+
+template <typename T, int LPR, bool HAS_P>
+__device__ __forceinline__ void lscoef_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
+                                              unsigned mask, const T (&xu)[4], const T (&pu)[4],
+                                              double (&t)[5]) {
+    double xx = 0, xp = 0, pp = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        xx += (double)xu[i] * (double)xu[i];
+        if (HAS_P) {
+            xp += (double)xu[i] * (double)pu[i];
+            pp += (double)pu[i] * (double)pu[i];
+        }
+    }
+    xx = gsum<LPR>(xx, mask);
+    if (HAS_P) {
+        xp = gsum<LPR>(xp, mask);
+        pp = gsum<LPR>(pp, mask);
+    }
+    const double ln = a.lambda * (double)n;
+    t[0] += ln * xx;
+    if (HAS_P) {
+        t[1] += ln * 2.0 * xp;
+        t[2] += ln * pp;
+    }
+    if (gl == 0) {
+        const int64_t o = a.rowoff + row;
+        const int nt = HAS_P ? 5 : 1;
+        for (int q = 0; q < nt; ++q) a.rowterm[q * a.stride + o] = t[q];
+    }
+}
+
+template <typename T, int LPR, bool HAS_P>
+__global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
+    const int lane = threadIdx.x & 31, gl = lane % LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const bool act = gl < a.ld / 4;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / LPR;
+    const T *Xs = reinterpret_cast<const T *>(a.Xs), *Ps = reinterpret_cast<const T *>(a.Ps);
+    const T *Xo = reinterpret_cast<const T *>(a.Xo), *Po = reinterpret_cast<const T *>(a.Po);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR; r < a.nrows; r += ngroups) {
+        const int64_t row = a.order[a.row_begin + r];
+        const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
+        T xu[4], pu[4];
+        if (act) {
+            ld4(Xs + row * a.ld + 4 * gl, xu);
+            if (HAS_P) ld4(Ps + row * a.ld + 4 * gl, pu); else zero4(pu);
+        } else {
+            zero4(xu); zero4(pu);
+        }
+        double t[5] = {0, 0, 0, 0, 0};
+        for (int64_t e = beg; e < beg + n; ++e)
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, t);
+        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
+    }
+}
+
+template <typename T, int LPR, bool HAS_P>
+__global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
+    constexpr int NG = 256 / LPR;
+    __shared__ double part[NG][5];
+    const int lane = threadIdx.x & 31, gl = lane % LPR, gi = threadIdx.x / LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const bool act = gl < a.ld / 4;
+    const T *Xs = reinterpret_cast<const T *>(a.Xs), *Ps = reinterpret_cast<const T *>(a.Ps);
+    const T *Xo = reinterpret_cast<const T *>(a.Xo), *Po = reinterpret_cast<const T *>(a.Po);
+    for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+        const int64_t row = a.order[a.row_begin + r];
+        const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
+        const int64_t seg = (n + NG - 1) / NG;
+        const int64_t e0 = beg + gi * seg, e1 = min(beg + n, e0 + seg);
+        T xu[4], pu[4];
+        if (act) {
+            ld4(Xs + row * a.ld + 4 * gl, xu);
+            if (HAS_P) ld4(Ps + row * a.ld + 4 * gl, pu); else zero4(pu);
+        } else {
+            zero4(xu); zero4(pu);
+        }
+        double t[5] = {0, 0, 0, 0, 0};
+        for (int64_t e = e0; e < e1; ++e)
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, t);
+        if (gl == 0)
+            for (int q = 0; q < 5; ++q) part[gi][q] = t[q];
+        __syncthreads();
+        if (gi == 0) {
+            double tot[5] = {0, 0, 0, 0, 0};
+            for (int q = 0; q < NG; ++q)
+                for (int s = 0; s < 5; ++s) tot[s] += part[q][s];
+            lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, tot);
+        }
+        __syncthreads();
+    }
+}
+
+// rows whose ratings are handled from the other side: only the lambda terms
+template <typename T, int LPR, bool HAS_P>
+__global__ void __launch_bounds__(256) k_lscoef_reg(PassArgs a) {
+    const int lane = threadIdx.x & 31, gl = lane % LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const bool act = gl < a.ld / 4;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / LPR;
+    const T *Xs = reinterpret_cast<const T *>(a.Xs), *Ps = reinterpret_cast<const T *>(a.Ps);
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR; row < a.nrows; row += ngroups) {
+        const int64_t n = a.ptr[row + 1] - a.ptr[row];
+        T xu[4], pu[4];
+        if (act) {
+            ld4(Xs + row * a.ld + 4 * gl, xu);
+            if (HAS_P) ld4(Ps + row * a.ld + 4 * gl, pu); else zero4(pu);
+        } else {
+            zero4(xu); zero4(pu);
+        }
+        double t[5] = {0, 0, 0, 0, 0};
+        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
+        if (HAS_P && gl == 0) {
+            a.rowterm[3 * a.stride + a.rowoff + row] = 0.0;
+            a.rowterm[4 * a.stride + a.rowoff + row] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reduction + scalar post-operations
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
+// Q(alpha) - Q(0), Horner form, no contraction
+__device__ double q_delta(const double *c, double al) {
+    double t = dadd(c[3], dmul(al, c[4]));
+    t = dadd(c[2], dmul(al, t));
+    t = dadd(c[1], dmul(al, t));
+    return dmul(al, t);
+}
+
+// Real roots of a x^3 + b x^2 + c x + d = 0 (Cardano / trigonometric form,
+// each polished by two Newton steps).  Returns the number of roots.
+__device__ int cubic_roots(double a, double b, double c, double d, double *r) {
+    int n = 0;
+    if (fabs(a) <= 1e-300) {
+        if (fabs(b) <= 1e-300) {
+            if (fabs(c) > 1e-300) r[n++] = -d / c;
+            return n;
+        }
+        const double disc = c * c - 4 * b * d;
+        if (disc >= 0) {
+            const double s = sqrt(disc);
+            const double q = -0.5 * (c + (c >= 0 ? s : -s));
+            r[n++] = q / b;
+            if (q != 0) r[n++] = d / q;
+        }
+        return n;
+    }
+    const double B = b / a, C = c / a, D = d / a;
+    const double p = C - B * B / 3.0, q = 2.0 * B * B * B / 27.0 - B * C / 3.0 + D;
+    const double disc = 0.25 * q * q + p * p * p / 27.0;
+    if (disc > 0) {
+        const double s = sqrt(disc);
+        r[n++] = cbrt(-0.5 * q + s) + cbrt(-0.5 * q - s) - B / 3.0;
+    } else if (p == 0) {
+        r[n++] = -B / 3.0;
+    } else {
+        const double m = 2.0 * sqrt(-p / 3.0);
+        double arg = 3.0 * q / (p * m);
+        arg = fmax(-1.0, fmin(1.0, arg));
+        const double th = acos(arg) / 3.0;
+        for (int k = 0; k < 3; ++k) r[n++] = m * cos(th - 2.0943951023931957 * k) - B / 3.0;
+    }
+    for (int i = 0; i < n; ++i) {
+        for (int it = 0; it < 2; ++it) {
+            const double x = r[i];
+            const double f = ((a * x + b) * x + c) * x + d, fp = (3 * a * x + 2 * b) * x + c;
+            if (fp != 0) r[i] = x - f / fp;
+        }
+    }
+    return n;
+}
+
+__device__ void post_lselect(double *S, const LsParams lp) {
+    const double *c = S + S_C;
+    double alpha = 0.0, dq = 0.0;
+    int ok = 0, k = 0;
+    if (c[1] < 0.0) {
+        if (lp.mode == ALS_LS_EXACT) {
+            double r[3];
+            const int n = cubic_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
+            double best = 0.0;
+            for (int i = 0; i < n; ++i) {
+                if (r[i] > 0.0) {
+                    const double v = q_delta(c, r[i]);
+                    if (!ok || v < best) { best = v; alpha = r[i]; ok = 1; }
+                }
+            }
+            dq = best;
+        } else {
+            alpha = lp.alpha0;
+            for (k = 0; k <= lp.max_shrinks; ++k) {
+                dq = q_delta(c, alpha);
+                const double rhs = dmul(dmul(alpha, lp.c), c[1]);
+                if (dq <= rhs) { ok = 1; break; }
+                alpha = dmul(alpha, lp.tau);
+            }
+            if (!ok) k = lp.max_shrinks;
+        }
+    }
+    if (ok) {
+        S[S_ALPHA] = alpha;
+        S[S_MODE] = 0.0;
+        S[S_F] = dadd(c[0], dq);
+    } else {
+        S[S_ALPHA] = 0.0;
+        S[S_MODE] = 1.0;
+        S[S_F] = __longlong_as_double(0x7ff8000000000000ll);  // unknown until evaluated
+        S[S_NFALL] += 1.0;
+    }
+    S[S_SHRINK] = (double)k;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const double *__restrict__ rowterm, int64_t n,
+                                                        int nterms, double *__restrict__ partial,
+                                                        unsigned *__restrict__ ticket, double *__restrict__ S,
+                                                        int s_off, int post, LsParams lp) {
+    __shared__ double red[RED_THREADS];
+    __shared__ bool last;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    for (int t = 0; t < nterms; ++t) {
+        double s = 0.0;
+        for (int64_t i = b0 + threadIdx.x; i < b1; i += RED_THREADS) s += rowterm[t * n + i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[t * RED_MAXB + blockIdx.x] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(ticket, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = 0; t < nterms; ++t) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += RED_THREADS) s += partial[t * RED_MAXB + i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) S[s_off + t] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
+        if (post == POST_LSELECT) {
+            post_lselect(S, lp);
+        } else if (post == POST_BETA) {
+            const double gg = S[s_off], gbg = S[s_off + 1], gbd = S[s_off + 2];
+            const double sk = S[S_S];
+            S[S_BETA] = (S[S_MODE] == 0.0 && sk != 0.0) ? gbd / sk : 0.0;
+            S[S_S] = gbg;
+            S[S_GG] = gg;
+        } else if (post == POST_INIT) {
+            S[S_GG] = S[s_off];
+            S[S_GG0] = S[s_off];
+            S[S_S] = S[s_off + 1];
+            S[S_MODE] = 0.0;
+            S[S_BETA] = 0.0;
+            S[S_NFALL] = 0.0;
+            S[S_ALPHA] = 0.0;
+            S[S_SHRINK] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vectors
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_update_x(T *__restrict__ X, const T *__restrict__ Xbar, const T *__restrict__ P,
+                           const double *__restrict__ S, int64_t n) {
+    const bool fallback = S[S_MODE] != 0.0;
+    const T al = (T)S[S_ALPHA];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[i] = fallback ? Xbar[i] : fma(al, P[i], X[i]);
+}
+
+template <typename T>
+__global__ void k_update_p(T *__restrict__ P, const T *__restrict__ Gbar, const double *__restrict__ S,
+                           int64_t n) {
+    const T be = (T)S[S_BETA];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        P[i] = fma(be, P[i], -Gbar[i]);
+}
+
+template <typename T>
+__global__ void k_neg(T *__restrict__ d, const T *__restrict__ s, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = -s[i];
+}
+
+// user layout (dtype S_, row stride nf) -> internal (T, row stride ld, zero pad)
+template <typename TS, typename TD>
+__global__ void k_convert(TD *__restrict__ dst, const TS *__restrict__ src, int64_t rows, int nf,
+                          int src_ld, int dst_ld) {
+    const int64_t n = rows * dst_ld;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / dst_ld;
+        const int k = (int)(i - r * dst_ld);
+        if (k < nf) dst[i] = (TD)src[r * src_ld + k];
+        else if (k < dst_ld) dst[i] = TD(0);
+    }
+}
+
+inline unsigned grid_for(als_ctx *c, int64_t n, int threads) {
+    const int64_t want = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)c->sm_count * 8;
+    return (unsigned)std::max<int64_t>(1, std::min(want, cap));
+}
+
+template <int LPR>
+struct Lpr {};
+
+inline int lpr_for(int ld) {
+    const int slots = ld / 4;
+    if (slots <= 4) return 4;
+    if (slots <= 8) return 8;
+    if (slots <= 16) return 16;
+    return 32;
+}
+
+template <typename T, int LPR>
+als_status grad_launch(als_ctx *c, const PassArgs &a, bool heavy) {
+    if (a.nrows <= 0) return ALS_OK;
+    if (heavy) {
+        const unsigned g = (unsigned)std::min<int64_t>(a.nrows, 65535);
+        k_grad_heavy<T, LPR><<<g, 256, 0, c->stream>>>(a);
+    } else {
+        const int64_t groups_per_block = 256 / LPR;
+        const int64_t want = (a.nrows + groups_per_block - 1) / groups_per_block;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * 8));
+        k_grad<T, LPR><<<g, 256, 0, c->stream>>>(a);
+    }
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+template <typename T, int LPR, bool HAS_P>
+als_status lscoef_launch(als_ctx *c, const PassArgs &a, int kind) {  // 0 rows, 1 heavy, 2 reg
+    if (a.nrows <= 0) return ALS_OK;
+    if (kind == 1) {
+        const unsigned g = (unsigned)std::min<int64_t>(a.nrows, 65535);
+        k_lscoef_heavy<T, LPR, HAS_P><<<g, 256, 0, c->stream>>>(a);
+    } else {
+        const int64_t groups_per_block = 256 / LPR;
+        const int64_t want = (a.nrows + groups_per_block - 1) / groups_per_block;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * 8));
+        if (kind == 0) k_lscoef<T, LPR, HAS_P><<<g, 256, 0, c->stream>>>(a);
+        else k_lscoef_reg<T, LPR, HAS_P><<<g, 256, 0, c->stream>>>(a);
+    }
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+template <typename T>
+als_status grad_dispatch(als_ctx *c, const PassArgs &a, bool heavy) {
+    switch (lpr_for(a.ld)) {
+        case 4: return grad_launch<T, 4>(c, a, heavy);
+        case 8: return grad_launch<T, 8>(c, a, heavy);
+        case 16: return grad_launch<T, 16>(c, a, heavy);
+        default: return grad_launch<T, 32>(c, a, heavy);
+    }
+}
+
+template <typename T, bool HAS_P>
+als_status lscoef_dispatch(als_ctx *c, const PassArgs &a, int kind) {
+    switch (lpr_for(a.ld)) {
+        case 4: return lscoef_launch<T, 4, HAS_P>(c, a, kind);
+        case 8: return lscoef_launch<T, 8, HAS_P>(c, a, kind);
+        case 16: return lscoef_launch<T, 16, HAS_P>(c, a, kind);
+        default: return lscoef_launch<T, 32, HAS_P>(c, a, kind);
+    }
+}
+
+}  // namespace
+
+als_status launch_grad(als_ctx *c, const PassArgs &a, bool heavy) {
+    return c->f64 ? grad_dispatch<double>(c, a, heavy) : grad_dispatch<float>(c, a, heavy);
+}
+
+als_status launch_lscoef(als_ctx *c, const PassArgs &a, bool heavy) {
+    const int kind = heavy ? 1 : 0;
+    if (a.Ps) return c->f64 ? lscoef_dispatch<double, true>(c, a, kind) : lscoef_dispatch<float, true>(c, a, kind);
+    return c->f64 ? lscoef_dispatch<double, false>(c, a, kind) : lscoef_dispatch<float, false>(c, a, kind);
+}
+
+als_status launch_lscoef_reg(als_ctx *c, const PassArgs &a) {
+    if (a.Ps) return c->f64 ? lscoef_dispatch<double, true>(c, a, 2) : lscoef_dispatch<float, true>(c, a, 2);
+    return c->f64 ? lscoef_dispatch<double, false>(c, a, 2) : lscoef_dispatch<float, false>(c, a, 2);
+}
+
+als_status launch_reduce(als_ctx *c, int nterms, int64_t n, int s_off, int post, const LsParams &lp) {
+    const int64_t want = (n + 8191) / 8192;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, RED_MAXB));
+    k_reduce<<<g, RED_THREADS, 0, c->stream>>>(c->rowterm, n, nterms, c->partial, c->ticket, c->S, s_off,
+                                               post, lp);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_update_x(als_ctx *c) {
+    const int64_t n = (c->n_u + c->n_m) * c->ld;
+    const unsigned g = grid_for(c, n, 256);
+    if (c->f64) k_update_x<double><<<g, 256, 0, c->stream>>>((double *)c->X, (const double *)c->Xbar, (const double *)c->P, c->S, n);
+    else k_update_x<float><<<g, 256, 0, c->stream>>>((float *)c->X, (const float *)c->Xbar, (const float *)c->P, c->S, n);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_update_p(als_ctx *c) {
+    const int64_t n = (c->n_u + c->n_m) * c->ld;
+    const unsigned g = grid_for(c, n, 256);
+    if (c->f64) k_update_p<double><<<g, 256, 0, c->stream>>>((double *)c->P, (const double *)c->Gbar, c->S, n);
+    else k_update_p<float><<<g, 256, 0, c->stream>>>((float *)c->P, (const float *)c->Gbar, c->S, n);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_neg_copy(als_ctx *c, void *dst, const void *src, size_t n) {
+    const unsigned g = grid_for(c, (int64_t)n, 256);
+    if (c->f64) k_neg<double><<<g, 256, 0, c->stream>>>((double *)dst, (const double *)src, (int64_t)n);
+    else k_neg<float><<<g, 256, 0, c->stream>>>((float *)dst, (const float *)src, (int64_t)n);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_convert_in(als_ctx *c, void *dst, const void *src, int64_t rows, int src_dtype, int src_ld) {
+    if (rows <= 0) return ALS_OK;
+    const unsigned g = grid_for(c, rows * c->ld, 256);
+    if (c->f64) {
+        if (src_dtype == ALS_DT_F64) k_convert<double, double><<<g, 256, 0, c->stream>>>((double *)dst, (const double *)src, rows, c->nf, src_ld, c->ld);
+        else k_convert<float, double><<<g, 256, 0, c->stream>>>((double *)dst, (const float *)src, rows, c->nf, src_ld, c->ld);
+    } else {
+        if (src_dtype == ALS_DT_F64) k_convert<double, float><<<g, 256, 0, c->stream>>>((float *)dst, (const double *)src, rows, c->nf, src_ld, c->ld);
+        else k_convert<float, float><<<g, 256, 0, c->stream>>>((float *)dst, (const float *)src, rows, c->nf, src_ld, c->ld);
+    }
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_convert_out(als_ctx *c, void *dst, const void *src, int64_t rows, int dst_dtype, int dst_ld) {
+    if (rows <= 0) return ALS_OK;
+    const unsigned g = grid_for(c, rows * dst_ld, 256);
+    if (c->f64) {
+        if (dst_dtype == ALS_DT_F64) k_convert<double, double><<<g, 256, 0, c->stream>>>((double *)dst, (const double *)src, rows, c->nf, c->ld, dst_ld);
+        else k_convert<double, float><<<g, 256, 0, c->stream>>>((float *)dst, (const double *)src, rows, c->nf, c->ld, dst_ld);
+    } else {
+        if (dst_dtype == ALS_DT_F64) k_convert<float, double><<<g, 256, 0, c->stream>>>((double *)dst, (const float *)src, rows, c->nf, c->ld, dst_ld);
+        else k_convert<float, float><<<g, 256, 0, c->stream>>>((float *)dst, (const float *)src, rows, c->nf, c->ld, dst_ld);
+    }
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+namespace {
+__global__ void k_check_requests(const int64_t *__restrict__ ptr, int64_t nreq, const int32_t *__restrict__ idx,
+                                 const float *__restrict__ val, int64_t total, int64_t bound, int *__restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride)
+        if (idx[e] < 0 || idx[e] >= bound || !isfinite(val[e])) atomicAdd(flag, 1);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nreq; q += stride)
+        if (ptr[q + 1] < ptr[q] || ptr[q + 1] > total) atomicAdd(flag, 1);
+}
+}  // namespace
+
+als_status launch_check_requests(als_ctx *c, const int64_t *ptr, int64_t nreq, const int32_t *idx, const float *val,
+                                 int64_t total, int64_t bound, int *flag) {
+    ALS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    const unsigned g = grid_for(c, std::max(total, nreq), 256);
+    k_check_requests<<<g, 256, 0, c->stream>>>(ptr, nreq, idx, val, total, bound, flag);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}

@@ -1,0 +1,297 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances: the FP64 form must match the oracle to 1e-10 relative in f and in
+the factors, per iteration; the mixed form must match the FP64 run's f to
+1e-5 relative at equal iteration count and its final train RMSE to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def _als():
+    from paper_1508_03110_gb300 import ALS
+    return ALS
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    r = synth.make_config("tiny")
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    return r, P, x0
+
+
+def _model(r, n_f=None, **kw):
+    return _als()(r.n_u, r.n_m, r.rows, r.cols, r.vals, n_f or r.n_f, r.lam, **kw)
+
+
+# -- builder (bit-exact) -----------------------------------------------------------
+
+def test_builder_matches_host_sort(tiny):
+    r, P, _ = tiny
+    with _model(r) as m:
+        R = m.ratings()
+    assert np.array_equal(R["uptr"], P.uptr)
+    assert np.array_equal(R["uidx"], P.uidx)
+    assert np.array_equal(R["uval"].astype(np.float64), P.uval)
+    assert np.array_equal(R["mptr"], P.mptr)
+    assert np.array_equal(R["midx"], P.midx)
+    assert np.array_equal(R["mval"].astype(np.float64), P.mval)
+    du = np.diff(P.uptr); dm = np.diff(P.mptr)
+    assert np.array_equal(R["uorder"], np.lexsort((np.arange(r.n_u), -du)))
+    assert np.array_equal(R["morder"], np.lexsort((np.arange(r.n_m), -dm)))
+
+
+def test_builder_from_csr_input(tiny):
+    r, P, x0 = tiny
+    o = np.lexsort((r.cols, r.rows))
+    rowptr = np.zeros(r.n_u + 1, np.int64)
+    np.cumsum(np.bincount(r.rows, minlength=r.n_u), out=rowptr[1:])
+    with _als()(r.n_u, r.n_m, None, r.cols[o], r.vals[o], r.n_f, r.lam, rowptr=rowptr) as m:
+        R = m.ratings()
+    assert np.array_equal(R["uidx"], P.uidx) and np.array_equal(R["midx"], P.midx)
+
+
+def test_builder_rejects_bad_input(tiny):
+    from paper_1508_03110_gb300 import ALSError
+    r, _, _ = tiny
+    rows = r.rows.copy(); rows[5] = r.n_u
+    with pytest.raises(ALSError, match="EINVAL"):
+        _als()(r.n_u, r.n_m, rows, r.cols, r.vals, r.n_f, r.lam)
+    vals = r.vals.copy(); vals[7] = np.nan
+    with pytest.raises(ALSError, match="EINVAL"):
+        _als()(r.n_u, r.n_m, r.rows, r.cols, vals, r.n_f, r.lam)
+    rows = np.concatenate([r.rows, r.rows[:1]]); cols = np.concatenate([r.cols, r.cols[:1]])
+    vals = np.concatenate([r.vals, r.vals[:1]])
+    with pytest.raises(ALSError, match="duplicate"):
+        _als()(r.n_u, r.n_m, rows, cols, vals, r.n_f, r.lam)
+    with pytest.raises(ALSError, match="EBUDGET"):
+        _als()(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, hbm_budget_bytes=1 << 16)
+
+
+# -- single operators (FP64) --------------------------------------------------------------
+
+def test_loss_grad_fp64(tiny):
+    r, P, x0 = tiny
+    with _model(r) as m:
+        m.set_x(x0)
+        assert m.loss() == pytest.approx(oracle.loss(P, x0), rel=1e-12)
+        g, gn = m.grad()
+        gref = oracle.grad(P, x0)
+        assert _rel(g, gref) < 1e-12
+        assert gn == pytest.approx(np.linalg.norm(gref), rel=1e-12)
+
+
+def test_linesearch_coeffs_fp64(tiny):
+    r, P, x0 = tiny
+    p = np.random.default_rng(3).normal(size=x0.shape[0]) * 0.1
+    with _model(r) as m:
+        m.set_x(x0)
+        c = m.linesearch_coeffs(p)
+    cref = oracle.ls_coeffs(P, x0, p)
+    assert np.allclose(c, cref, rtol=1e-11, atol=1e-11 * abs(cref[0]))
+
+
+def test_sweep_fp64(tiny):
+    r, P, x0 = tiny
+    with _model(r) as m:
+        m.set_x(x0)
+        m.sweep(1)
+        x1 = m.get_x()
+    assert _rel(x1, oracle.sweep(P, x0)) < TOL64
+
+
+def test_als_trajectory_fp64(tiny):
+    """Algorithm 1, 50 sweeps: f and x per sweep within 1e-10 of the oracle."""
+    r, P, x0 = tiny
+    ref = oracle.als(P, x0, 50, with_grad=False)
+    with _model(r) as m:
+        m.set_x(x0)
+        for k in range(50):
+            m.sweep(1)
+            if k % 5 == 4 or k < 3:
+                x = m.get_x()
+                assert _rel(x, ref[k].x) < TOL64, k
+                assert m.loss() == pytest.approx(ref[k].f, rel=TOL64)
+
+
+def test_alsncg_trajectory_fp64(tiny):
+    """Algorithm 2, 50 iterations: f, |g| and x per iteration within 1e-10."""
+    r, P, x0 = tiny
+    ref = oracle.alsncg(P, x0, 50)
+    with _model(r) as m:
+        m.set_x(x0)
+        for k in range(50):
+            info = m.step()
+            x = m.get_x()
+            assert info["shrinks"] == ref[k].shrinks or ref[k].margin < 1e-9, k
+            assert _rel(x, ref[k].x) < TOL64, (k, _rel(x, ref[k].x))
+            assert info["f"] == pytest.approx(ref[k].f, rel=TOL64), k
+            assert info["gnorm"] == pytest.approx(ref[k].gnorm, rel=1e-8), k
+
+
+@pytest.mark.parametrize("n_f", [1, 3, 7, 20, 33, 64, 100])
+def test_alsncg_various_nf_fp64(tiny, n_f):
+    r, _, _ = tiny
+    P = oracle.build_problem(r.n_u, r.n_m, n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 5)
+    ref = oracle.alsncg(P, x0, 3)
+    with _model(r, n_f=n_f) as m:
+        m.set_x(x0)
+        for k in range(3):
+            m.step()
+        assert _rel(m.get_x(), ref[-1].x) < TOL64
+
+
+def test_exact_line_search_variant(tiny):
+    r, P, x0 = tiny
+    ref = oracle.alsncg(P, x0, 5, mode="exact")
+    with _model(r, ls_mode="exact") as m:
+        m.set_x(x0)
+        for k in range(5):
+            info = m.step()
+        assert _rel(m.get_x(), ref[-1].x) < 1e-8
+        assert info["alpha"] == pytest.approx(ref[-1].alpha, rel=1e-8)
+
+
+def test_graph_run_equals_steps(tiny):
+    r, P, x0 = tiny
+    with _model(r) as m:
+        m.set_x(x0)
+        for _ in range(7):
+            m.step(info=False)
+        xa = m.get_x()
+        m.set_x(x0)
+        out = m.run(7, 0.0, check_every=3)
+        xb = m.get_x()
+    assert out["iters"] == 7
+    assert np.array_equal(xa, xb)
+
+
+def test_determinism(tiny):
+    r, _, x0 = tiny
+    xs = []
+    for _ in range(2):
+        with _model(r, precision="mixed") as m:
+            m.set_x(x0)
+            m.run(5)
+            xs.append(m.get_x())
+    assert np.array_equal(xs[0], xs[1])
+
+
+# -- edge cases ------------------------------------------------------------------
+
+def _edge_problem():
+    """Empty items, degree-1 rows, heavy rows (>= 2048 ratings) on both sides."""
+    rng = np.random.default_rng(0)
+    n_u, n_m = 300, 2600
+    rows, cols = [], []
+    for i in range(n_u):
+        if i < 3:
+            d = 2300 + 50 * i            # heavy users
+        elif i < 10:
+            d = 1
+        else:
+            d = int(rng.integers(2, 40))
+        c = rng.choice(n_m - 5, size=d, replace=False)   # last 5 items: empty
+        rows.append(np.full(d, i)); cols.append(c)
+    rows = np.concatenate(rows); cols = np.concatenate(cols)
+    # one heavy item: rated by every user
+    extra = np.setdiff1d(np.arange(n_u), rows[cols == 7])
+    rows = np.concatenate([rows, extra]); cols = np.concatenate([cols, np.full(extra.size, 7)])
+    vals = (np.round(2 * np.clip(rng.normal(3.5, 1, rows.size), 0.5, 5)) / 2).astype(np.float32)
+    return n_u, n_m, rows.astype(np.int32), cols.astype(np.int32), vals
+
+
+@pytest.mark.parametrize("n_f", [5, 40])
+def test_edge_cases_fp64(n_f):
+    n_u, n_m, rows, cols, vals = _edge_problem()
+    P = oracle.build_problem(n_u, n_m, n_f, 0.05, rows, cols, vals)
+    x0 = synth.init_factors(n_u, n_m, n_f, 2)
+    p = np.random.default_rng(1).normal(size=x0.shape[0])
+    with _als()(n_u, n_m, rows, cols, vals, n_f, 0.05) as m:
+        m.set_x(x0)
+        assert m.loss() == pytest.approx(oracle.loss(P, x0), rel=1e-12)
+        g, _ = m.grad()
+        assert _rel(g, oracle.grad(P, x0)) < 1e-12
+        assert np.allclose(m.linesearch_coeffs(p), oracle.ls_coeffs(P, x0, p), rtol=1e-11)
+        ref = oracle.alsncg(P, x0, 4)
+        for k in range(4):
+            m.step()
+        x = m.get_x()
+        assert _rel(x, ref[-1].x) < TOL64
+        assert np.all(x.reshape(-1, n_f)[n_u + n_m - 5:] == 0.0)   # empty items held at 0
+
+
+# -- fold-in ------------------------------------------------------------------
+
+def test_foldin_fp64(tiny):
+    r, P, x0 = tiny
+    ptr, items, vals = synth.foldin_requests(40, r.n_m, 1, 600, seed=5)
+    ptr = np.concatenate([ptr, [ptr[-1]]])   # plus one empty request
+    M = x0[r.n_u * r.n_f:]
+    with _model(r) as m:
+        m.set_x(x0)
+        u = m.foldin(ptr, items, vals)
+    ref = oracle.foldin(r.n_f, r.lam, M, ptr, items, vals.astype(np.float64))
+    assert _rel(u, ref) < TOL64
+    assert np.all(u[-1] == 0)
+
+
+def test_foldin_rejects_bad_ids(tiny):
+    from paper_1508_03110_gb300 import ALSError
+    r, _, x0 = tiny
+    with _model(r) as m:
+        m.set_x(x0)
+        with pytest.raises(ALSError, match="EINVAL"):
+            m.foldin(np.array([0, 2]), np.array([1, r.n_m]), np.array([3.0, 4.0]))
+
+
+# -- mixed precision ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_f", [10, 40, 100])
+def test_mixed_matches_fp64_run(tiny, n_f):
+    """Mixed form: f within 1e-5 of the FP64 GPU run at equal iteration count,
+    final train RMSE within 1e-4."""
+    r, _, _ = tiny
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 7)
+    fs = {}
+    xs = {}
+    for prec in ("fp64", "mixed"):
+        with _model(r, n_f=n_f, precision=prec) as m:
+            m.set_x(x0)
+            fs[prec] = []
+            for k in range(30):
+                fs[prec].append(m.step()["f"])
+            xs[prec] = m.get_x()
+    f64, fmx = np.array(fs["fp64"]), np.array(fs["mixed"])
+    assert np.all(np.abs(fmx - f64) <= 1e-5 * np.abs(f64)), np.max(np.abs(fmx - f64) / np.abs(f64))
+
+    def rmse(x):
+        U = x[:r.n_u * n_f].reshape(r.n_u, n_f); M = x[r.n_u * n_f:].reshape(r.n_m, n_f)
+        e = r.vals - np.einsum("ij,ij->i", U[r.rows], M[r.cols])
+        return float(np.sqrt(np.mean(e ** 2)))
+    assert abs(rmse(xs["mixed"]) - rmse(xs["fp64"])) < 1e-4
+
+
+def test_mixed_sweep_close_to_oracle(tiny):
+    r, P, x0 = tiny
+    with _model(r, precision="mixed") as m:
+        m.set_x(x0)
+        m.sweep(3)
+        x = m.get_x()
+    ref = x0
+    for _ in range(3):
+        ref = oracle.sweep(P, ref)
+    assert _rel(x, ref) < 1e-5

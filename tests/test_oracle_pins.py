@@ -336,3 +336,12 @@ def test_thread_count_does_not_change_results():
     assert a[0] == b[0]
     for u, v in zip(a[1:], b[1:]):
         assert np.array_equal(u, v)
+
+
+def test_solve_rows_equals_half_sweep_rows():
+    P, x = _small_problem(n_u=30, n_m=20, n_f=4)
+    k = P.n_u * P.n_f
+    U = oracle.half_sweep(P, 0, x[k:]).reshape(P.n_u, P.n_f)
+    M = oracle.half_sweep(P, 1, x[:k]).reshape(P.n_m, P.n_f)
+    assert np.array_equal(oracle.solve_rows(P, 0, x[k:], [3, 0, 29]), U[[3, 0, 29]])
+    assert np.array_equal(oracle.solve_rows(P, 1, x[:k], [19, 2]), M[[19, 2]])
