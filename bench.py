@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the ALS-NCG hot path on one GB300 (or N independent replicas).
+
+A step is one ALS-NCG iteration (Algorithm 2): the one-pass line-search
+coefficients and Algorithm 3, the update of x, one ALS sweep (Gram build,
+Cholesky, solves, refinement) on both sides, the two gradient passes with the
+fused beta inner products, and the new direction -- every kernel of the hot
+path, replayed as a CUDA graph.  The default workload is the
+MovieLens-20M-shaped synthetic problem (138,493 users x 26,744 items, 2e7
+ratings, n_f = 100, lambda = 0.05) in mixed precision.
+
+value  = ratings x iterations / second over the timed steps, summed over ranks
+         (inputs resident in HBM before the timed region starts);
+e2e    = the same metric through the C ABI with host buffers: building the
+         context from host COO arrays, setting x_0 from the host, the
+         iterations, and reading the factors back, all inside the timed region;
+roofline = the fused sweep kernel (the dominant launch) against the measured
+         peak of the unit that bounds it;
+cpu_baseline = the FP64 oracle on the host cores, on a bounded sample.
+
+`--impl reference` times the oracle alone (the reference arm of this build).
+Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N` runs N independent
+replicas (the method needs no exchange on one GPU), value is
+the sum over ranks and the time the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mixed ALS-NCG vs FP64 ALS s-to-tol, same GPU; ratings/s/sweep; fold-in p99"
+UNIT = "ratings/s (ratings x ALS-NCG iterations per second)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ml20m")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--gram", default="auto", choices=["auto", "fma", "tc"])
+    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1])); mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sweep_flops(r, n_f, refine, precision):
+    """Algorithmic FLOPs of one ALS sweep (both halves), per the method:
+    symmetric Gram 2 * nnz * n_f (n_f + 1) (n_f (n_f+1)/2 FMAs per rating and
+    half), Cholesky n_f^3 / 3 and triangular solves 2 n_f^2 per row and solve,
+    the right-hand side (FP64) or the matrix-free residual (mixed, 4 n_f per
+    rating and refinement) per half."""
+    rows = r.n_u + r.n_m
+    gram = 2.0 * r.nnz * n_f * (n_f + 1)
+    chol = rows * n_f ** 3 / 3.0
+    if precision == "fp64":
+        return gram + chol + rows * 2 * n_f ** 2 + 2.0 * r.nnz * 2 * n_f
+    return gram + chol + refine * (rows * 2 * n_f ** 2 + 2.0 * r.nnz * 4 * n_f)
+
+
+def oracle_sample(r, x0, budget, rng_seed=0):
+    """Time the FP64 oracle on a bounded sample of one ALS-NCG iteration and
+    scale it to the whole iteration: the sweep on a systematic sample of rows
+    (every s-th row in degree order, both sides), plus the full gradient and
+    Q-coefficient passes.  Returns (seconds per full iteration, description, threads)."""
+    import oracle
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    k = r.n_u * r.n_f
+    t = time.perf_counter(); g = oracle.grad(P, x0); t_grad = time.perf_counter() - t
+    t = time.perf_counter(); oracle.ls_coeffs(P, x0, g); t_ls = time.perf_counter() - t
+    du, dm = np.diff(P.uptr), np.diff(P.mptr)
+    ou, om = np.argsort(-du, kind="stable"), np.argsort(-dm, kind="stable")
+    frac = 0.002
+    t_u = t_m = 0.0
+    su = sm = 1
+    for _ in range(6):
+        su = max(1, int(1 / frac)); sm = su
+        t = time.perf_counter(); oracle.solve_rows(P, 0, x0[k:], ou[::su]); t_u = time.perf_counter() - t
+        t = time.perf_counter(); oracle.solve_rows(P, 1, x0[:k], om[::sm]); t_m = time.perf_counter() - t
+        spent = t_u + t_m + t_grad + t_ls
+        if spent > 0.25 * budget or frac >= 0.05:
+            break
+        frac = min(0.05, frac * max(2.0, 0.5 * budget / max(spent, 1e-3)))
+    est = t_u * r.n_u / len(ou[::su]) + t_m * r.n_m / len(om[::sm]) + t_grad + t_ls
+    desc = (f"one FP64 ALS-NCG iteration on the same workload: the sweep timed on every {su}-th row "
+            f"in degree order ({len(ou[::su])} users, {len(om[::sm])} items) and scaled to all rows, "
+            f"plus the full gradient and Q-coefficient passes")
+    return est, desc, oracle.get_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import synth
+    r = synth.make_config(args.workload)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    times = []
+    desc, thr = "", 1
+    budget = max(3.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        est, desc, thr = oracle_sample(r, x0, budget)
+        if i >= args.warmup:
+            times.append(est)
+    t = float(np.mean(times)) if times else float("nan")
+    value = r.nnz / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args, r), "precision": "fp64 (oracle)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def workload_name(args, r):
+    return (f"{args.workload}: synthetic {r.n_u:,} users x {r.n_m:,} items, {r.nnz:,} ratings, "
+            f"n_f={r.n_f}, lambda={r.lam}")
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        return
+    import torch
+    import synth
+    from paper_1508_03110_gb300 import ALS
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    peaks, peak_src = load_peaks()
+    r = synth.make_config(args.workload)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    stream = torch.cuda.Stream()
+    kw = dict(precision=args.precision, refine_steps=args.refine, gram_path=args.gram, stream=stream)
+    m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, **kw)
+    m.set_x(x0)
+    m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
+
+    # ---- timed region: K ALS-NCG iterations (graph replays) ----
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    info = m.run(args.steps, 0.0, check_every=args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    barrier()
+    clocks = sampler.stop()
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = r.nnz * args.steps * world / t
+    launches = int(info["kernels"])
+
+    # ---- the dominant kernel: the fused sweep (U half + M half launches) ----
+    reps = 5
+    m.sweep(1)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    m.sweep(reps)
+    s1.record(stream)
+    s1.synchronize()
+    t_sweep = s0.elapsed_time(s1) / 1e3 / reps
+    fl = sweep_flops(r, r.n_f, args.refine, args.precision)
+    use_tc = args.precision == "mixed" and (args.gram == "tc")
+    if use_tc:
+        peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
+        achieved = 2.0 * r.nnz * 128 * 112 * 2 / t_sweep / 1e12
+        peak_note = f"bf16 dense, {peak_src} (burst)"
+    else:
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        if args.precision == "fp64":
+            peak = 1.25
+            peak_note = "FP64 nominal 1.25 TFLOP/s (GB300)"
+        else:
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+            peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+        unit, bound = "TFLOP/s", "alu"
+        achieved = fl / t_sweep / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel": "k_sweep (fused Gram+Cholesky+solve)",
+                "peak_source": peak_note, "sweep_ms": t_sweep * 1e3}
+    m.close()
+
+    extra = {}
+    # ---- FP64 sweep time on the same workload (plain FP64 ALS per-iteration cost) ----
+    if not args.no_fp64 and rank == 0:
+        m64 = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision="fp64", stream=stream)
+        m64.set_x(x0)
+        m64.sweep(1)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        m64.sweep(1)
+        s1.record(stream)
+        s1.synchronize()
+        extra["fp64_als_sweep_ms"] = s0.elapsed_time(s1)
+        m64.close()
+
+    # ---- e2e: the whole job through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        rows, cols, vals = np.ascontiguousarray(r.rows), np.ascontiguousarray(r.cols), np.ascontiguousarray(r.vals)
+        t0 = time.perf_counter()
+        me = ALS(r.n_u, r.n_m, rows, cols, vals, r.n_f, r.lam, **kw)
+        me.set_x(x0)
+        me.run(args.steps, 0.0, check_every=args.steps)
+        U, M = me.get_factors()
+        te = time.perf_counter() - t0
+        me.close()
+        if dist is not None:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        h2d = r.nnz * 12 + x0.nbytes
+        d2h = U.nbytes + M.nbytes
+        e2e = {"value": r.nnz * args.steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "includes": "context build from host COO, x0 upload, K iterations, factor download"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        est, desc, thr = oracle_sample(r, x0, args.cpu_budget)
+        cpu = {"value": r.nnz / est, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.precision == "fp64" else ("bf16+f32" if use_tc else "f32"),
+               "data": "synthetic",
+               "config": {"workload": workload_name(args, r), "precision": args.precision,
+                          "gram": args.gram, "refine_steps": args.refine,
+                          "l2": "inputs larger than L2 (ratings stored twice: 320 MB; vectors 66 MB each)"},
+               "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "e2e": e2e,
+               "cpu_baseline": cpu, "final_gnorm_rel": info["gnorm"] / info["gnorm0"], **extra}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,8 @@ typedef struct {
                            alpha passed); the direction restarted            */
     int64_t fallbacks;  /* total fallbacks so far                            */
     int64_t notspd;     /* rows whose system was not SPD so far              */
+    int64_t kernels;    /* kernel launches issued by the call that filled
+                           this record (iterations run as CUDA graphs)      */
 } als_iter_info;
 
 /* Fill *cfg with the paper's defaults: alpha0 = 10, tau = 0.9, c = 0.5
@@ -149,6 +151,18 @@ ALS_API als_status als_set_factors(als_ctx *ctx, const void *U, const void *M, i
 /* Copy x out into U (n_u x n_f) and M (n_m x n_f).  Synchronous for host
  * destinations. */
 ALS_API als_status als_get_factors(als_ctx *ctx, void *U, void *M, int dtype, int on_device);
+
+/* Algorithm 2 state, for checkpoint / resume and lockstep checks.  Vectors are
+ * n_u + n_m rows of n_f (dtype, on_device): x_k, p_k, g_k = grad f(x_k),
+ * gbar_k = x_k - P(x_k) and xbar_k = P(x_k).  scalars[4] = { gbar_k . g_k,
+ * |g_0|^2, k, fallbacks so far }.  als_get_state fails with ALS_EINVAL before
+ * Algorithm 2 has started; als_set_state makes the next alsncg_step continue
+ * from the given state.  Synchronous for host buffers. */
+ALS_API als_status als_get_state(als_ctx *ctx, void *x, void *p, void *g, void *gbar, void *xbar,
+                                 double scalars[4], int dtype, int on_device);
+ALS_API als_status als_set_state(als_ctx *ctx, const void *x, const void *p, const void *g,
+                                 const void *gbar, const void *xbar, const double scalars[4],
+                                 int dtype, int on_device);
 
 /* Algorithm 1: n_sweeps times x <- P(x): all u_i by Eq. (3) from M, then all
  * m_j by Eq. (4) from the new U.  Asynchronous. */

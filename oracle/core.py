@@ -274,6 +274,8 @@ class IterRecord:
     shrinks: int = 0
     margin: float = float("inf")
     c: np.ndarray = None
+    state: dict = None   # p_k, gbar_k, xbar_k, s_k after this iteration (Algorithm 2)
+    g: np.ndarray = None
 
 
 def ncg(x0, grad_fn, precond_fn, step_fn, iters, on_iter=None):
@@ -310,7 +312,8 @@ def ncg(x0, grad_fn, precond_fn, step_fn, iters, on_iter=None):
         g, gbar = g_new, gbar_new
         if on_iter is not None:
             on_iter(k, x, g, dict(alpha=ls.alpha, beta=beta, fallback=not ls.ok,
-                                  shrinks=ls.shrinks, margin=ls.margin))
+                                  shrinks=ls.shrinks, margin=ls.margin,
+                                  state=dict(p=p, gbar=gbar, xbar=xbar, s=s)))
     return x
 
 
@@ -329,8 +332,11 @@ def alsncg(P: Problem, x0, iters, alpha0=10.0, tau=0.9, cc=0.5, max_shrinks=200,
         return backtracking(c, alpha0, tau, cc, max_shrinks)
 
     def on_iter(k, x, g, info):
+        if not keep_x:
+            info = dict(info, state=None)
         recs.append(IterRecord(k=k + 1, x=x.copy() if keep_x else None, f=loss(P, x),
-                               gnorm=float(np.linalg.norm(g)), c=last_c.get("c"), **info))
+                               gnorm=float(np.linalg.norm(g)), c=last_c.get("c"),
+                               g=g.copy() if keep_x else None, **info))
 
     ncg(x0, lambda x: grad(P, x), lambda x: sweep(P, x), step, iters, on_iter)
     return recs

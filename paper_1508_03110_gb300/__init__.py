@@ -28,7 +28,7 @@ def _torch():
 def info_dict(info: IterInfo) -> dict:
     return dict(k=info.k, f=info.f, gnorm=info.gnorm, gnorm0=info.gnorm0, alpha=info.alpha,
                 beta=info.beta, c=list(info.c), shrinks=info.shrinks, fallback=bool(info.fallback),
-                fallbacks=info.fallbacks, notspd=info.notspd)
+                fallbacks=info.fallbacks, notspd=info.notspd, kernels=info.kernels)
 
 
 class _Buf:
@@ -182,6 +182,23 @@ class ALS:
     def get_x(self):
         U, M = self.get_factors()
         return np.concatenate([U.reshape(-1), M.reshape(-1)])
+
+    def get_state(self):
+        """Algorithm 2 state: dict of x, p, g, gbar, xbar (float64, flat) and scalars."""
+        n = (self.n_u + self.n_m) * self.n_f
+        v = {k: np.empty(n, np.float64) for k in ("x", "p", "g", "gbar", "xbar")}
+        sc = (ctypes.c_double * 4)()
+        _lib.check(self.lib.als_get_state(self.ctx, v["x"].ctypes.data, v["p"].ctypes.data, v["g"].ctypes.data,
+                                          v["gbar"].ctypes.data, v["xbar"].ctypes.data, sc, ALS_DT_F64, 0),
+                   "als_get_state")
+        v.update(s=sc[0], gg0=sc[1], k=int(sc[2]), fallbacks=int(sc[3]))
+        return v
+
+    def set_state(self, x, p, g, gbar, xbar, s, gg0, k=0, fallbacks=0):
+        arrs = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in (x, p, g, gbar, xbar)]
+        sc = (ctypes.c_double * 4)(float(s), float(gg0), float(k), float(fallbacks))
+        _lib.check(self.lib.als_set_state(self.ctx, *[a.ctypes.data for a in arrs], sc, ALS_DT_F64, 0),
+                   "als_set_state")
 
     # -- algorithms -------------------------------------------------------------
     def sweep(self, n=1):

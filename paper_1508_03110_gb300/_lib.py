@@ -39,7 +39,7 @@ class IterInfo(ctypes.Structure):
         ("k", ctypes.c_int64), ("f", ctypes.c_double), ("gnorm", ctypes.c_double),
         ("gnorm0", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
         ("c", ctypes.c_double * 5), ("shrinks", ctypes.c_int32), ("fallback", ctypes.c_int32),
-        ("fallbacks", ctypes.c_int64), ("notspd", ctypes.c_int64),
+        ("fallbacks", ctypes.c_int64), ("notspd", ctypes.c_int64), ("kernels", ctypes.c_int64),
     ]
 
 
@@ -52,6 +52,8 @@ SIGNATURES = {
     "als_get_ratings": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "als_set_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "als_get_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "als_get_state": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_dbl), _i32, _i32]),
+    "als_set_state": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_dbl), _i32, _i32]),
     "als_sweep": (_i32, [_vp, _i32]),
     "alsncg_step": (_i32, [_vp, ctypes.POINTER(IterInfo)]),
     "alsncg_run": (_i32, [_vp, _i32, _dbl, _i32, ctypes.POINTER(IterInfo), ctypes.POINTER(_i32)]),

@@ -236,6 +236,7 @@ void fill_info(const als_ctx *c, als_iter_info *o) {
     o->fallback = S[S_MODE] != 0.0;
     o->fallbacks = (int64_t)S[S_NFALL];
     o->notspd = c->hflags[0];
+    o->kernels = 0;
 }
 
 als_status loss_now(als_ctx *c, double *f) {
@@ -271,6 +272,16 @@ als_status capture_graphs(als_ctx *c) {
             als_set_error(std::string("graph capture: ") + cudaGetErrorString(e));
             return ALS_ECUDA;
         }
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        int64_t nk = 0;
+        for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+        }
+        c->graph_kernels[p] = nk;
         const cudaError_t e2 = cudaGraphInstantiate(&c->graph[p], g, 0);
         cudaGraphDestroy(g);
         if (e2 != cudaSuccess) {
@@ -465,6 +476,61 @@ extern "C" als_status als_get_factors(als_ctx *c, void *U, void *M, int dtype, i
     return ALS_OK;
 }
 
+extern "C" als_status als_get_state(als_ctx *c, void *x, void *p, void *g, void *gbar, void *xbar,
+                                    double scalars[4], int dtype, int on_device) {
+    if (!c || !valid_dtype(dtype)) { als_set_error("als_get_state: bad argument"); return ALS_EINVAL; }
+    if (!c->ncg_ready) { als_set_error("als_get_state: ALS-NCG has not started"); return ALS_EINVAL; }
+    const int64_t rows = c->n_u + c->n_m;
+    const size_t bytes = (size_t)rows * c->nf * dtype_size(dtype);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    void *src[5] = {c->X, c->P, c->G[c->gcur], c->Gbar, c->Xbar};
+    void *dst[5] = {x, p, g, gbar, xbar};
+    for (int i = 0; i < 5; ++i) {
+        if (!dst[i]) continue;
+        als_status s = launch_convert_out(c, c->tmpvec, src[i], rows, dtype, c->nf);
+        if (s != ALS_OK) return s;
+        ALS_CUDA_TRY(cudaMemcpyAsync(dst[i], c->tmpvec, bytes, kind, c->stream));
+        if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    als_status s = read_scalars(c);
+    if (s != ALS_OK) return s;
+    if (scalars) {
+        scalars[0] = c->hS[S_S];
+        scalars[1] = c->hS[S_GG0];
+        scalars[2] = (double)c->k;
+        scalars[3] = c->hS[S_NFALL];
+    }
+    return ALS_OK;
+}
+
+extern "C" als_status als_set_state(als_ctx *c, const void *x, const void *p, const void *g, const void *gbar,
+                                    const void *xbar, const double scalars[4], int dtype, int on_device) {
+    if (!c || !x || !p || !g || !gbar || !xbar || !scalars || !valid_dtype(dtype)) {
+        als_set_error("als_set_state: bad argument");
+        return ALS_EINVAL;
+    }
+    const int64_t rows = c->n_u + c->n_m;
+    const size_t bytes = (size_t)rows * c->nf * dtype_size(dtype);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const void *src[5] = {x, p, g, gbar, xbar};
+    void *dst[5] = {c->X, c->P, c->G[c->gcur], c->Gbar, c->Xbar};
+    for (int i = 0; i < 5; ++i) {
+        ALS_CUDA_TRY(cudaMemcpyAsync(c->tmpvec, src[i], bytes, kind, c->stream));
+        als_status s = launch_convert_in(c, dst[i], c->tmpvec, rows, dtype, c->nf);
+        if (s != ALS_OK) return s;
+        if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    const double hs[4] = {scalars[0], scalars[1], scalars[3], 0.0};
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_S, &hs[0], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_GG0, &hs[1], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_NFALL, &hs[2], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_MODE, &hs[3], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->k = (int64_t)scalars[2];
+    c->ncg_ready = true;
+    return ALS_OK;
+}
+
 extern "C" als_status als_sweep(als_ctx *c, int32_t n_sweeps) {
     if (!c || n_sweeps < 0) { als_set_error("als_sweep: bad argument"); return ALS_EINVAL; }
     for (int i = 0; i < n_sweeps; ++i) {
@@ -482,14 +548,17 @@ extern "C" als_status alsncg_step(als_ctx *c, als_iter_info *out) {
         s = ncg_init(c);
         if (s != ALS_OK) return s;
     }
-    s = ncg_iter(c, c->gcur);
+    s = capture_graphs(c);
     if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaGraphLaunch(c->graph[c->gcur], c->stream));
+    const int64_t nk = c->graph_kernels[c->gcur];
     c->gcur ^= 1;
     c->k += 1;
     if (out) {
         s = read_scalars(c);
         if (s != ALS_OK) return s;
         fill_info(c, out);
+        out->kernels = nk;
         if (out->fallback) {
             double f;
             s = loss_now(c, &f);
@@ -511,9 +580,11 @@ extern "C" als_status alsncg_run(als_ctx *c, int32_t max_iter, double rel_tol, i
     s = capture_graphs(c);
     if (s != ALS_OK) return s;
     int32_t done = 0;
+    int64_t nk = 0;
     bool converged = false;
     while (done < max_iter && !converged) {
         ALS_CUDA_TRY(cudaGraphLaunch(c->graph[c->gcur], c->stream));
+        nk += c->graph_kernels[c->gcur];
         c->gcur ^= 1;
         c->k += 1;
         ++done;
@@ -528,6 +599,7 @@ extern "C" als_status alsncg_run(als_ctx *c, int32_t max_iter, double rel_tol, i
         s = read_scalars(c);
         if (s != ALS_OK) return s;
         fill_info(c, last);
+        last->kernels = nk;
     }
     return ALS_OK;
 }

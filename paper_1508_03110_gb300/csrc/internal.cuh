@@ -89,6 +89,7 @@ struct als_ctx {
     bool use_tc = false;
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};   // kernel nodes per captured iteration
 };
 
 #define RED_MAXB 512

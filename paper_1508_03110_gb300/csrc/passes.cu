@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
 template <typename T, int LPR, bool HAS_P>
 __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4], const T *Xo,
                                               const T *Po, int64_t j, float r, int ld, int gl,
-                                              bool act, unsigned mask, double (&t)[5]) {
+                                              bool act, unsigned mask, bool own, double (&t)[5]) {
     T xm[4], pm[4];
     if (act) {
         ld4(Xo + j * ld + 4 * gl, xm);
@@ -219,15 +219,24 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
         const T d1 = gsum<LPR>(dot4(xu, pm), mask);
         const T d2 = gsum<LPR>(dot4(pu, xm), mask);
         const T d3 = gsum<LPR>(dot4(pu, pm), mask);
+        // the FP64 terms of this rating are accumulated by one lane of the
+        // group (round robin), not redundantly by all of them
+        if (!own) return;
         const double aa = (double)d1 + (double)d2, b = (double)d3;
         t[0] += e0 * e0;
         t[1] += -2.0 * e0 * aa;
         t[2] += aa * aa - 2.0 * e0 * b;
         t[3] += 2.0 * aa * b;
         t[4] += b * b;
-    } else {
+    } else if (own) {
         t[0] += e0 * e0;
     }
+}
+
+template <int LPR>
+__device__ __forceinline__ void tsum5(double (&t)[5], unsigned mask) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) t[q] = gsum<LPR>(t[q], mask);
 }
 
 template <typename T, int LPR, bool HAS_P>
@@ -280,8 +289,12 @@ __global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
             zero4(xu); zero4(pu);
         }
         double t[5] = {0, 0, 0, 0, 0};
-        for (int64_t e = beg; e < beg + n; ++e)
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, t);
+        int owner = 0;
+        for (int64_t e = beg; e < beg + n; ++e) {
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner == gl, t);
+            owner = owner + 1 == LPR ? 0 : owner + 1;
+        }
+        tsum5<LPR>(t, mask);
         lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
     }
 }
@@ -308,8 +321,12 @@ __global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
             zero4(xu); zero4(pu);
         }
         double t[5] = {0, 0, 0, 0, 0};
-        for (int64_t e = e0; e < e1; ++e)
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, t);
+        int owner = 0;
+        for (int64_t e = e0; e < e1; ++e) {
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner == gl, t);
+            owner = owner + 1 == LPR ? 0 : owner + 1;
+        }
+        tsum5<LPR>(t, mask);
         if (gl == 0)
             for (int q = 0; q < 5; ++q) part[gi][q] = t[q];
         __syncthreads();
