@@ -196,6 +196,33 @@ ALS_API als_status als_grad(als_ctx *ctx, void *g_out_or_null, int dtype, int on
 ALS_API als_status als_linesearch_coeffs(als_ctx *ctx, const void *p_or_null, int dtype,
                                  int on_device, double c[5]);
 
+/* Allocation-free variant of als_linesearch_coeffs (the paper has no
+ * counterpart: it is an interface for callers that must not allocate).
+ * Callers that cannot call cudaMalloc at this point -- code running while a
+ * stream is captured into a CUDA graph, a framework that owns all device
+ * memory through its own pool, a serving loop that must never enter an
+ * allocator -- get the five coefficients of Q(alpha) = f(x + alpha p) without
+ * a context.  Every argument is caller-owned device memory: uptr[n_u+1],
+ * uidx[nnz], uval[nnz] (ratings by user, any order within a user), mptr[n_m+1]
+ * (by-item row pointers; only the item degrees n_mj are read), x and p with
+ * n_u + n_m rows of `ld` values (ld a multiple of 4, n_f <= ld <= 128,
+ * padding zero) of the given dtype, and c_out[5] (double) which receives
+ * c0..c4.  Work is enqueued on `stream` (NULL: legacy default stream) and
+ * the call returns without synchronising.
+ * The scratch (per-row FP64 terms and reduction partials) is a fixed device
+ * array inside the library, held by every GPU that loads it until the
+ * process exits; it limits n_u + n_m to 262,144 (ALS_EINVAL beyond).  The
+ * first call on each device looks up that array's device address (a one-time
+ * set-up, not an allocation): make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race on
+ * it and give wrong results; order them (one stream).  Nothing here calls
+ * cudaMalloc, cudaFree or any allocating routine. */
+ALS_API als_status als_linesearch_coeffs_static(int64_t n_u, int64_t n_m, int32_t n_f, int32_t ld,
+                                                double lambda, const int64_t *uptr,
+                                                const int32_t *uidx, const float *uval,
+                                                const int64_t *mptr, const void *x, const void *p,
+                                                int dtype, double *c_out, void *stream);
+
 /* Fold-in: for each of n_req new users with ratings items/vals[req_ptr[q] ..
  * req_ptr[q+1]) solve Eq. (3) against the context's current M, i.e.
  * u = (M_I M_I^T + lambda |I| I)^-1 M_I r.  u_out: n_req x n_f (dtype,

@@ -60,6 +60,8 @@ SIGNATURES = {
     "als_loss": (_i32, [_vp, ctypes.POINTER(_dbl)]),
     "als_grad": (_i32, [_vp, _vp, _i32, _i32, ctypes.POINTER(_dbl)]),
     "als_linesearch_coeffs": (_i32, [_vp, _vp, _i32, _i32, ctypes.POINTER(_dbl)]),
+    "als_linesearch_coeffs_static": (_i32, [_i64, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
+                                            _i32, _vp, _vp]),
     "als_foldin": (_i32, [_vp, _i64, _vp, _vp, _vp, _i32, _vp, _i32, _i32]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
