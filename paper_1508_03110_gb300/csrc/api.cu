@@ -108,6 +108,7 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.lambda = c->cfg.lambda;
     a.refine = c->cfg.refine_steps;
     a.notspd = c->dflags;
+    a.timeout = c->dflags + 7;
     if (c->use_tc) {
         als_status s = launch_to_bf16(c, F, side ? c->n_u : c->n_m, c->f64);
         if (s != ALS_OK) return s;
@@ -188,6 +189,10 @@ als_status read_scalars(als_ctx *c) {
     ALS_CUDA_TRY(cudaMemcpyAsync(c->hS, c->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->hflags[7]) {
+        als_set_error("a bounded device wait of the tensor-core sweep expired; results are not valid");
+        return ALS_ETIMEOUT;
+    }
     return ALS_OK;
 }
 
@@ -366,7 +371,7 @@ extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m
         }
         c->own_stream = true;
     }
-    c->use_tc = false;
+    c->use_tc = !c->f64 && c->nf > 32 && cfg->gram_path != ALS_GRAM_FMA;
     if (cfg->gram_path == ALS_GRAM_TC && c->f64) { als_set_error("als_create: the tensor-core Gram needs ALS_MIXED"); return fail(ALS_EINVAL); }
     if (cfg->gram_path == ALS_GRAM_TC) c->use_tc = true;
 
@@ -396,7 +401,7 @@ extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m
     ALLOC(c->dflags, 16 * sizeof(int));
     if (c->use_tc) {
         c->shadow_rows = std::max(n_u, n_m);
-        ALLOC(c->shadow, (size_t)c->shadow_rows * ALS_TC_LD * sizeof(__nv_bfloat16));
+        ALLOC(c->shadow, (size_t)c->shadow_rows * 2 * ALS_TC_LD * sizeof(__nv_bfloat16));
     }
 #undef ALLOC
     if (cudaMallocHost(&c->hS, S_COUNT * sizeof(double)) != cudaSuccess ||
@@ -723,6 +728,7 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     a.lambda = c->cfg.lambda;
     a.refine = c->cfg.refine_steps + 1;  // cold start: one more correction
     a.notspd = c->dflags + 5;
+    a.timeout = c->dflags + 7;
     if (c->use_tc) {
         s = launch_to_bf16(c, a.F, c->n_m, c->f64);
         if (s != ALS_OK) { cleanup(); return s; }

@@ -132,6 +132,7 @@ struct SweepArgs {
     double lambda;
     int refine;
     int *notspd;
+    int *timeout;           // set when a bounded device wait expired
 };
 als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
 als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64);

@@ -214,14 +214,14 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
         zero4(xm); zero4(pm);
     }
     const T d0 = gsum<LPR>(dot4(xu, xm), mask);
-    const double e0 = (double)r - (double)d0;
     if (HAS_P) {
         const T d1 = gsum<LPR>(dot4(xu, pm), mask);
         const T d2 = gsum<LPR>(dot4(pu, xm), mask);
         const T d3 = gsum<LPR>(dot4(pu, pm), mask);
-        // the FP64 terms of this rating are accumulated by one lane of the
-        // group (round robin), not redundantly by all of them
+        // the FP64 terms of this rating (conversions included: FP64 issue is
+        // scarce on this GPU) are formed by one lane of the group, round robin
         if (!own) return;
+        const double e0 = (double)r - (double)d0;
         const double aa = (double)d1 + (double)d2, b = (double)d3;
         t[0] += e0 * e0;
         t[1] += -2.0 * e0 * aa;
@@ -229,6 +229,7 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
         t[3] += 2.0 * aa * b;
         t[4] += b * b;
     } else if (own) {
+        const double e0 = (double)r - (double)d0;
         t[0] += e0 * e0;
     }
 }

@@ -181,26 +181,36 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
     const size_t smem = (size_t)G * group_smem_elems<T>(a.nf) * sizeof(T);
     auto kern = k_sweep_fma<T, TPR, MAXE, WARM>;
     ALS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ALS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     int occ = 0;
     ALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem));
     if (occ < 1) {
         als_set_error("sweep: the row working set does not fit in shared memory");
         return ALS_ENOTSUP;
     }
+    // one row group per CTA: the hardware packs as many CTAs per SM as fit
     const int64_t want = (a.nrows + G - 1) / G;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * c->sm_count));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)INT32_MAX));
     kern<<<grid, 128, smem, c->stream>>>(a);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
 
+// Two-term BF16 shadow of the fixed side for the tensor-core Gram: row r is
+// [hi(128) | lo2(128)] with hi = bf16(f), lo2 = bf16(2 (f - hi)); f - hi is
+// exact in FP32 and the factor 2 is exact, so f = hi + lo2 / 2 to ~2^-17.
 template <typename T>
 __global__ void k_to_bf16(const T *__restrict__ F, int64_t rows, int ld, __nv_bfloat16 *__restrict__ out) {
     const int64_t n = rows * ALS_TC_LD;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / ALS_TC_LD;
         const int k = (int)(i - r * ALS_TC_LD);
-        out[i] = __float2bfloat16_rn(k < ld ? (float)F[r * ld + k] : 0.0f);
+        const float f = k < ld ? (float)F[r * ld + k] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+        const float lo2 = 2.0f * (f - __bfloat162float(hi));
+        out[r * (2 * ALS_TC_LD) + k] = hi;
+        out[r * (2 * ALS_TC_LD) + ALS_TC_LD + k] = __float2bfloat16_rn(lo2);
     }
 }
 

@@ -86,3 +86,141 @@ __device__ void sw_trisolve(const T *A, int ldA, int nf, const T *diag, T *b, T 
     }
     sw_gsync<TPR>();
 }
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky (panels of 16 columns) for n <= 128, FP32,
+// by a CTA of exactly 128 threads.  Panel: thread t holds row kb+t of the
+// panel in registers, one column at a time (pivot, scale, rank-1 update of
+// the panel).  Trailing update A22 -= L21 L21^T with 4x4 register blocks
+// from the transposed panel PT in shared memory.
+// A: lower triangle used; on return its lower triangle holds L (diagonal
+// included) and diag[k] = 1 / L[k][k] (reciprocal, for the solves).  work: >= 16*128 + 256 + 2 floats, 16-byte
+// aligned.  Returns false (in every thread) on a non-positive pivot.
+__device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float *diag, float *work, int t) {
+    float *PT = work;              // [16][128]
+    float *lcol = work + 16 * 128; // [2][128]
+    float *piv = lcol + 256;       // [2]
+    for (int kb = 0; kb < n; kb += 16) {
+        const int nb = min(16, n - kb), mp = n - kb;
+        float row[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) row[c] = (t < mp && c < nb) ? A[(kb + t) * ldA + kb + c] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            if (c < nb) {
+                if (t == c) piv[c & 1] = row[c];
+                __syncthreads();
+                const float p = piv[c & 1];
+                if (!(p > 0.0f)) return false;
+                const float rd = rsqrtf(p);   // 1 / L[k][k]
+                float l = 0.0f;
+                if (t > c && t < mp) {
+                    l = row[c] * rd;
+                    row[c] = l;
+                }
+                if (t == c) {
+                    row[c] = p * rd;
+                    diag[kb + c] = rd;
+                }
+                lcol[(c & 1) * 128 + t] = l;
+                __syncthreads();
+                if (t > c && t < mp) {
+#pragma unroll
+                    for (int cc = c + 1; cc < 16; ++cc) row[cc] -= l * lcol[(c & 1) * 128 + cc];
+                }
+            }
+        }
+        if (t < mp) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < nb && c <= t) A[(kb + t) * ldA + kb + c] = row[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) PT[c * 128 + t] = (t < mp && c < nb && t > c) ? row[c] : 0.0f;
+        __syncthreads();
+        const int m = mp - nb;
+        if (m > 0) {
+            const int mb = (m + 3) >> 2, nblk = mb * (mb + 1) / 2;
+            for (int bidx = t; bidx < nblk; bidx += 128) {
+                int bi = (int)((sqrtf(8.0f * (float)bidx + 1.0f) - 1.0f) * 0.5f);
+                while ((bi + 1) * (bi + 2) / 2 <= bidx) ++bi;
+                while (bi * (bi + 1) / 2 > bidx) --bi;
+                const int bj = bidx - bi * (bi + 1) / 2;
+                const int pi = nb + 4 * bi, pj = nb + 4 * bj;
+                float acc[4][4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float4 li = *reinterpret_cast<const float4 *>(PT + c * 128 + pi);
+                    const float4 lj = *reinterpret_cast<const float4 *>(PT + c * 128 + pj);
+                    const float a4[4] = {li.x, li.y, li.z, li.w}, b4[4] = {lj.x, lj.y, lj.z, lj.w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a4[p], b4[q], acc[p][q]);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int i = kb + pi + p;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = kb + pj + q;
+                        if (i < n && j <= i) A[i * ldA + j] -= acc[p][q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// L L^T x = b with L from chol_blocked128 (diag = reciprocals), blocks of 16: the diagonal block
+// is solved by warp 0 with shuffles, the rows outside it are updated by all
+// 128 threads.  b is consumed; z is scratch; x receives the solution (x may
+// alias z).
+__device__ __forceinline__ void trisolve_blocked128(const float *A, int ldA, int n, const float *diag, float *b,
+                                                    float *z, float *x, int t) {
+    const int warp = t >> 5, lane = t & 31;
+    for (int kb = 0; kb < n; kb += 16) {
+        const int nb = min(16, n - kb);
+        __syncthreads();
+        if (warp == 0) {
+            float bv = lane < nb ? b[kb + lane] : 0.0f;
+            for (int c = 0; c < nb; ++c) {
+                const float zc = __shfl_sync(0xffffffffu, bv, c) * diag[kb + c];
+                if (lane == c) z[kb + c] = zc;
+                if (lane > c && lane < nb) bv -= A[(kb + lane) * ldA + kb + c] * zc;
+            }
+        }
+        __syncthreads();
+        for (int i = kb + nb + t; i < n; i += 128) {
+            float s = 0.0f;
+            for (int c = 0; c < nb; ++c) s = fmaf(A[i * ldA + kb + c], z[kb + c], s);
+            b[i] -= s;
+        }
+    }
+    const int last = ((n - 1) / 16) * 16;
+    for (int kb = last; kb >= 0; kb -= 16) {
+        const int nb = min(16, n - kb);
+        __syncthreads();
+        if (warp == 0) {
+            float zv = lane < nb ? z[kb + lane] : 0.0f;
+            for (int c = nb - 1; c >= 0; --c) {
+                const float xc = __shfl_sync(0xffffffffu, zv, c) * diag[kb + c];
+                if (lane == c) x[kb + c] = xc;
+                if (lane < c) zv -= A[(kb + c) * ldA + kb + lane] * xc;
+            }
+        }
+        __syncthreads();
+        for (int i = t; i < kb; i += 128) {
+            float s = 0.0f;
+            for (int c = 0; c < nb; ++c) s = fmaf(A[(kb + c) * ldA + i], x[kb + c], s);
+            z[i] -= s;
+        }
+    }
+    __syncthreads();
+}

@@ -1,7 +1,307 @@
-// Placeholder for the tensor-core Gram path; replaced below.
+// Mixed-precision half sweep with the Gram matrices on the 5th-generation
+// tensor cores (tcgen05, sm_103a).
+//
+// For each row i (one CTA of 4 warps per row, 4 CTAs per SM), with the fixed
+// side F kept in a BF16 shadow of 128 columns:
+//   1. gather: each factor row is held as two BF16 rows, hi = bf16(f) and
+//      lo2 = bf16(2 (f - hi)); the rows of the row's ratings, 32 per chunk,
+//      are copied with cp.async into two 128-byte-swizzled, MN-major shared
+//      tiles H and L (rating k of the chunk is K index k, the factor index is
+//      the M/N index);
+//   2. Gram: one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//      M = 128, N = round_up(n_f, 16), K = 16 per instruction): D += H H^T
+//      and D += H L^T, so D = sum_e hi_e (hi_e + 2 lo_e)^T accumulates in
+//      TMEM; its symmetric part is sum_e (hi hi^T + hi lo^T + lo hi^T), the
+//      Gram matrix with ~2^-17 relative error (the lo lo^T term is dropped).
+//      Chunks are double buffered; tcgen05.commit on an mbarrier releases a
+//      stage;
+//   3. tcgen05.ld moves D into FP32 shared memory (row m of D is TMEM lane
+//      m), A = (D + D^T)/2 + lambda n_i I;
+//   4. blocked Cholesky of A and the refinement of the ALS solve from the
+//      current row: res = sum_e f_e (r_e - f_e . u) - lambda n_i u in FP32
+//      from the FP32 factors, u <- u + A^{-1} res (blocked triangular solves).
+// Every mbarrier wait is bounded (%globaltimer): on expiry the CTA records a
+// timeout, waits for its copies, frees its TMEM and returns.
 #include "internal.cuh"
+#include "sweep_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int KCH = 32;                          // ratings per chunk
+constexpr int TILE_BYTES = KCH * ALS_TC_LD * 2;  // 8 KB: one BF16 tile (H or L)
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;      // H and L
+constexpr int NSTAGE = 2;
+constexpr uint32_t LBO = 1024;  // byte distance between the two 64-wide MN atoms
+constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int TMEM_COLS = 128;
+
+struct TcLayout {
+    int ring, A, vec, mbar, holder, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int nf) {
+    TcLayout L;
+    L.ring = 0;
+    L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
+    int big = NSTAGE * STAGE_BYTES;
+    const int a_bytes = nf * (nf + 1) * 4;
+    if (a_bytes > big) big = a_bytes;
+    big = (big + 15) & ~15;
+    L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
+    L.mbar = L.vec + (5 * 128 + 2320) * 4;
+    L.holder = L.mbar + 16;
+    L.total = L.holder + 16;
+    return L;
+}
+
+__device__ __forceinline__ void ld4f(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+__device__ __forceinline__ float wsum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    unsigned char *base = smem_raw + pad;
+    const uint32_t sbase = raw + pad;
+    const int nf = a.nf, ldA = nf + 1;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const TcLayout L = tc_layout(nf);
+    float *A = reinterpret_cast<float *>(base + L.A);
+    float *vec = reinterpret_cast<float *>(base + L.vec);
+    float *colk = vec, *v1 = vec + 128, *v2 = vec + 256, *u = vec + 384, *diag = vec + 512;
+    float *part = vec + 640;   // residual partials (residual phase)
+    float *work = vec + 640;   // Cholesky panel scratch (factorisation phase)
+    const uint32_t mbar[2] = {sbase + L.mbar, sbase + L.mbar + 8};
+    uint32_t *holder = reinterpret_cast<uint32_t *>(base + L.holder);
+
+    if (t == 0) {
+        mbar_init(mbar[0], 1);
+        mbar_init(mbar[1], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(sbase + L.holder, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    const uint32_t idesc = idesc_bf16_f32_mn((uint32_t)ntc);
+    const float *F = reinterpret_cast<const float *>(a.F);
+    const __nv_bfloat16 *Fb = a.Fbf;
+    uint32_t phase[2] = {0u, 0u};
+    bool bail = false;
+
+    for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+        const int64_t row = a.order ? a.order[r] : r;
+        const int64_t beg = a.ptr[row];
+        const int n = (int)(a.ptr[row + 1] - beg);
+        const float *xi = a.Xin ? reinterpret_cast<const float *>(a.Xin) + row * a.ld : nullptr;
+        float *xo = reinterpret_cast<float *>(a.Xout) + row * a.ld;
+        float *gb = a.Gbar ? reinterpret_cast<float *>(a.Gbar) + row * a.ld : nullptr;
+        const float lam_n = (float)(a.lambda * (double)n);
+        bool ok = n > 0;
+        if (ok) {
+            // ---- 1-2. gather + tensor-core Gram -------------------------------
+            const int nch = (n + KCH - 1) / KCH;
+            int pend[2] = {0, 0};
+            auto gather = [&](int ch, int st) {
+                const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
+                const int64_t e0 = beg + (int64_t)ch * KCH, e_end = beg + n;
+#pragma unroll
+                for (int i = 0; i < (2 * KCH * 16) / TC_THREADS; ++i) {
+                    const int p = t + TC_THREADS * i;
+                    const int part_ = p >> 9, k = (p >> 4) & (KCH - 1), q = p & 15;
+                    const uint32_t dst = stage + part_ * TILE_BYTES + (k >> 3) * SBO + (q >> 3) * LBO + (k & 7) * 128 +
+                                         ((uint32_t)((q & 7) ^ (k & 7)) << 4);
+                    if (e0 + k < e_end) {
+                        const int64_t j = a.idx[e0 + k];
+                        cp_async16(dst, Fb + j * (2 * ALS_TC_LD) + part_ * ALS_TC_LD + q * 8);
+                    } else {
+                        cp_async16_zero(dst, Fb);
+                    }
+                }
+                cp_async_commit();
+            };
+            gather(0, 0);
+            for (int ch = 0; ch < nch; ++ch) {
+                const int st = ch & 1;
+                if (ch + 1 < nch) {
+                    const int sn = st ^ 1;
+                    if (pend[sn]) {  // the MMAs of chunk ch-1 still read stage sn
+                        const bool w = mbar_wait_bounded(mbar[sn], phase[sn], WAIT_NS);
+                        if (__syncthreads_or(!w)) { bail = true; break; }
+                        phase[sn] ^= 1u;
+                        pend[sn] = 0;
+                    }
+                    gather(ch + 1, sn);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (t == 0) {
+                    tc_fence_after();
+                    const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
+#pragma unroll
+                    for (int s = 0; s < KCH / 16; ++s) {
+                        const uint64_t dh = smem_desc_sw128(stage + (uint32_t)s * 2u * SBO, LBO, SBO);
+                        const uint64_t dl = smem_desc_sw128(stage + TILE_BYTES + (uint32_t)s * 2u * SBO, LBO, SBO);
+                        tc_mma_bf16(tmem, dh, dh, idesc, (ch > 0 || s > 0) ? 1u : 0u);
+                        tc_mma_bf16(tmem, dh, dl, idesc, 1u);
+                    }
+                    tc_commit(mbar[st]);
+                }
+                pend[st] = 1;
+            }
+            if (bail) break;
+            for (int s = 0; s < 2; ++s) {
+                if (pend[s]) {
+                    const bool w = mbar_wait_bounded(mbar[s], phase[s], WAIT_NS);
+                    if (__syncthreads_or(!w)) { bail = true; break; }
+                    phase[s] ^= 1u;
+                    pend[s] = 0;
+                }
+            }
+            if (bail) break;
+            tc_fence_after();
+            // ---- 3. TMEM -> FP32 A (row m of D is TMEM lane m) -----------------
+            {
+                const int m = 32 * warp + lane;
+                for (int c0 = 0; c0 < ntc; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                    if (m < nf) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int col = c0 + i;
+                            if (col < nf) A[m * ldA + col] = v[i];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // symmetric part of D, lower triangle, plus lambda n I
+            if (t < nf) {
+                for (int c = 0; c < t; ++c) A[t * ldA + c] = 0.5f * (A[t * ldA + c] + A[c * ldA + t]);
+                A[t * ldA + t] += lam_n;
+            }
+            __syncthreads();
+            // ---- 4. Cholesky, refinement from the current row ------------------
+            ok = chol_blocked128(A, ldA, nf, diag, work, t);
+            if (!ok && t == 0) atomicAdd(a.notspd, 1);
+        }
+        if (ok) {
+            for (int k = t; k < nf; k += TC_THREADS) u[k] = xi ? xi[k] : 0.0f;
+            for (int s = 0; s < a.refine; ++s) {
+                __syncthreads();
+                float uu[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) uu[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
+                const bool act = 4 * lane < a.ld;
+                int64_t e = beg + warp;
+                for (; e + 12 < beg + n; e += 16) {
+                    float f[4][4];
+                    int64_t j[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) j[q] = a.idx[e + 4 * q];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (act) ld4f(F + j[q] * a.ld + 4 * lane, f[q]);
+                        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.f;
+                    }
+                    float d[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        d[q] = uu[0] * f[q][0];
+#pragma unroll
+                        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float er = a.val[e + 4 * q] - d[q];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc[i] = fmaf(er, f[q][i], acc[i]);
+                    }
+                }
+                for (; e < beg + n; e += 4) {
+                    const int64_t j0 = a.idx[e];
+                    float f0[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (act) ld4f(F + j0 * a.ld + 4 * lane, f0);
+                    float d0 = uu[0] * f0[0];
+#pragma unroll
+                    for (int i = 1; i < 4; ++i) d0 = fmaf(uu[i], f0[i], d0);
+                    d0 = wsum(d0);
+                    const float e0 = a.val[e] - d0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] = fmaf(e0, f0[i], acc[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i];
+                __syncthreads();
+                if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
+                trisolve_blocked128(A, ldA, nf, diag, v1, v2, colk, t);
+                for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
+            }
+        } else {
+            for (int k = t; k < nf; k += TC_THREADS) u[k] = (n > 0 && xi) ? xi[k] : 0.0f;
+        }
+        __syncthreads();
+        for (int k = t; k < a.ld; k += TC_THREADS) {
+            const float uk = k < nf ? u[k] : 0.0f;
+            const float xk = xi ? xi[k] : 0.0f;
+            xo[k] = uk;
+            if (gb) gb[k] = xk - uk;
+        }
+        __syncthreads();
+    }
+    // ---- teardown: no copies in flight, TMEM returned -------------------------
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (bail && t == 0) atomicAdd(a.timeout, 1);
+}
+
+}  // namespace
+
 als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
-    (void)c; (void)a;
-    als_set_error("tensor-core Gram path not built");
-    return ALS_ENOTSUP;
+    if (a.nrows <= 0) return ALS_OK;
+    if (a.nf > ALS_TC_LD) {
+        als_set_error("sweep: the tensor-core Gram supports n_f <= 128");
+        return ALS_ENOTSUP;
+    }
+    const int ntc = (a.nf + 15) / 16 * 16;
+    const TcLayout L = tc_layout(a.nf);
+    // 46..56 KB of shared memory per CTA keeps exactly 4 CTAs (4 x 128 TMEM
+    // columns = the SM's 512) resident per SM, so tcgen05.alloc never waits.
+    size_t smem = (size_t)L.total + 1024;
+    if (smem < 46 * 1024) smem = 46 * 1024;
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the whole L1/shared array as shared memory, so that 4 CTAs fit per SM
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    // One CTA per row (rows in degree-descending order): the hardware keeps as
+    // many CTAs resident per SM as shared memory allows (at most 4 here), and
+    // each one holds its TMEM columns only for the row it solves.
+    const int64_t grid = std::min<int64_t>(a.nrows, (int64_t)INT32_MAX);
+    k_sweep_tc<<<(unsigned)grid, TC_THREADS, smem, c->stream>>>(a, ntc);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
 }

@@ -344,3 +344,48 @@ def test_mixed_sweep_close_to_oracle(tiny):
     for _ in range(3):
         ref = oracle.sweep(P, ref)
     assert _rel(x, ref) < 1e-5
+
+
+# -- tensor-core Gram (mixed, n_f > 32) ------------------------------------------------
+
+@pytest.mark.parametrize("n_f", [48, 100, 128])
+def test_tc_sweep_agrees_with_fp32_gram(tiny, n_f):
+    """The BF16 tensor-core Gram is the preconditioner of a refinement against
+    the FP32 residual: with enough refinement steps the sweep converges to the
+    same rows as the FP32-Gram path (and the FP64 oracle)."""
+    r, _, _ = tiny
+    P = oracle.build_problem(r.n_u, r.n_m, n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 3)
+    ref = oracle.sweep(P, x0)
+    out = {}
+    for path, refine in (("tc", 1), ("fma", 1), ("tc", 4)):
+        with _model(r, n_f=n_f, precision="mixed", gram_path=path, refine_steps=refine) as m:
+            m.set_x(x0)
+            m.sweep(1)
+            out[(path, refine)] = m.get_x()
+    assert _rel(out[("fma", 1)], ref) < 1e-5
+    assert _rel(out[("tc", 1)], ref) < 5e-2
+    assert _rel(out[("tc", 4)], ref) < 1e-5
+
+
+def test_tc_foldin_converges(tiny):
+    r, _, _ = tiny
+    n_f = 100
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 3)
+    ptr, items, vals = synth.foldin_requests(30, r.n_m, 1, 800, seed=9)
+    ref = oracle.foldin(n_f, r.lam, x0[r.n_u * n_f:], ptr, items, vals.astype(np.float64))
+    with _model(r, n_f=n_f, precision="mixed", gram_path="tc", refine_steps=5) as m:
+        m.set_x(x0)
+        u = m.foldin(ptr, items, vals)
+    assert _rel(u, ref) < 1e-5
+
+
+def test_tc_alsncg_converges(tiny):
+    r, _, _ = tiny
+    n_f = 64
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 3)
+    with _model(r, n_f=n_f, precision="mixed", gram_path="tc") as m:
+        m.set_x(x0)
+        out = m.run(40)
+    assert out["gnorm"] < 1e-3 * out["gnorm0"]
+    assert out["notspd"] == 0
