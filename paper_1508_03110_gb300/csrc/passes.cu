@@ -72,8 +72,11 @@ __device__ __forceinline__ V gsum(V x, unsigned mask) {
 
 template <int LPR>
 __device__ __forceinline__ unsigned group_mask(int lane) {
-    if (LPR == 32) return 0xffffffffu;
-    return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
+    if constexpr (LPR == 32) {
+        return 0xffffffffu;
+    } else {
+        return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -202,10 +205,39 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
 // ---------------------------------------------------------------------------
 // line-search coefficients (and the loss when Ps == Po == null)
 // ---------------------------------------------------------------------------
+// One rating's four dot products are reduced over the group; lane `owner`
+// parks them (in the storage precision) and every LPR ratings the whole group
+// turns its parked values into FP64 terms at once.  A warp-wide FP64
+// instruction costs the FP64 pipe the same whether 1 or 32 lanes are active,
+// so this keeps the FP64 instruction count at ~12 per LPR ratings.
+template <typename T>
+struct LsPending {
+    T r, d0, d1, d2, d3;
+    bool have;
+};
+
+template <typename T, bool HAS_P>
+__device__ __forceinline__ void ls_flush(LsPending<T> &q, double (&t)[5]) {
+    if (!q.have) return;
+    const double e0 = (double)q.r - (double)q.d0;
+    if (HAS_P) {
+        const double aa = (double)q.d1 + (double)q.d2, b = (double)q.d3;
+        t[0] += e0 * e0;
+        t[1] += -2.0 * e0 * aa;
+        t[2] += aa * aa - 2.0 * e0 * b;
+        t[3] += 2.0 * aa * b;
+        t[4] += b * b;
+    } else {
+        t[0] += e0 * e0;
+    }
+    q.have = false;
+}
+
 template <typename T, int LPR, bool HAS_P>
 __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4], const T *Xo,
                                               const T *Po, int64_t j, float r, int ld, int gl,
-                                              bool act, unsigned mask, bool own, double (&t)[5]) {
+                                              bool act, unsigned mask, int &owner, LsPending<T> &q,
+                                              double (&t)[5]) {
     T xm[4], pm[4];
     if (act) {
         ld4(Xo + j * ld + 4 * gl, xm);
@@ -214,23 +246,19 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
         zero4(xm); zero4(pm);
     }
     const T d0 = gsum<LPR>(dot4(xu, xm), mask);
+    T d1 = T(0), d2 = T(0), d3 = T(0);
     if (HAS_P) {
-        const T d1 = gsum<LPR>(dot4(xu, pm), mask);
-        const T d2 = gsum<LPR>(dot4(pu, xm), mask);
-        const T d3 = gsum<LPR>(dot4(pu, pm), mask);
-        // the FP64 terms of this rating (conversions included: FP64 issue is
-        // scarce on this GPU) are formed by one lane of the group, round robin
-        if (!own) return;
-        const double e0 = (double)r - (double)d0;
-        const double aa = (double)d1 + (double)d2, b = (double)d3;
-        t[0] += e0 * e0;
-        t[1] += -2.0 * e0 * aa;
-        t[2] += aa * aa - 2.0 * e0 * b;
-        t[3] += 2.0 * aa * b;
-        t[4] += b * b;
-    } else if (own) {
-        const double e0 = (double)r - (double)d0;
-        t[0] += e0 * e0;
+        d1 = gsum<LPR>(dot4(xu, pm), mask);
+        d2 = gsum<LPR>(dot4(pu, xm), mask);
+        d3 = gsum<LPR>(dot4(pu, pm), mask);
+    }
+    if (owner == gl) {
+        q.r = (T)r; q.d0 = d0; q.d1 = d1; q.d2 = d2; q.d3 = d3;
+        q.have = true;
+    }
+    if (++owner == LPR) {
+        owner = 0;
+        ls_flush<T, HAS_P>(q, t);
     }
 }
 
@@ -291,10 +319,11 @@ __global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
         }
         double t[5] = {0, 0, 0, 0, 0};
         int owner = 0;
-        for (int64_t e = beg; e < beg + n; ++e) {
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner == gl, t);
-            owner = owner + 1 == LPR ? 0 : owner + 1;
-        }
+        LsPending<T> q;
+        q.have = false;
+        for (int64_t e = beg; e < beg + n; ++e)
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
+        ls_flush<T, HAS_P>(q, t);
         tsum5<LPR>(t, mask);
         lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
     }
@@ -323,10 +352,11 @@ __global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
         }
         double t[5] = {0, 0, 0, 0, 0};
         int owner = 0;
-        for (int64_t e = e0; e < e1; ++e) {
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner == gl, t);
-            owner = owner + 1 == LPR ? 0 : owner + 1;
-        }
+        LsPending<T> q;
+        q.have = false;
+        for (int64_t e = e0; e < e1; ++e)
+            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
+        ls_flush<T, HAS_P>(q, t);
         tsum5<LPR>(t, mask);
         if (gl == 0)
             for (int q = 0; q < 5; ++q) part[gi][q] = t[q];

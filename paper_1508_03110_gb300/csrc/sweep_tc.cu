@@ -17,9 +17,11 @@
 //      stage;
 //   3. tcgen05.ld moves D into FP32 shared memory (row m of D is TMEM lane
 //      m), A = (D + D^T)/2 + lambda n_i I;
-//   4. blocked Cholesky of A and the refinement of the ALS solve from the
-//      current row: res = sum_e f_e (r_e - f_e . u) - lambda n_i u in FP32
-//      from the FP32 factors, u <- u + A^{-1} res (blocked triangular solves).
+//   4. blocked Cholesky of A (inverted diagonal blocks) and the refinement of
+//      the ALS solve from the current row u0 = x_i: res = sum_e f_e (r_e -
+//      f_e . u) - lambda n_i u in FP32 from the FP32 factors, u <- u +
+//      A^{-1} res.  The first residual (at u0) is gathered inside the Gram
+//      loop, while the chunk's copies and MMAs are in flight.
 // Every mbarrier wait is bounded (%globaltimer): on expiry the CTA records a
 // timeout, waits for its copies, frees its TMEM and returns.
 #include "internal.cuh"
@@ -68,6 +70,53 @@ __device__ __forceinline__ float wsum(float x) {
     return x;
 }
 
+// acc += sum over e in {e0, e0+4, e0+8, ...} < e1 of f_e (r_e - f_e . u): the
+// FP32 residual of the row's normal equations, one warp, lane = 4-wide slot;
+// four gathered rows in flight at a time.
+__device__ __forceinline__ void resid_range(const SweepArgs &a, const float *F, const float (&uu)[4], int64_t e,
+                                            int64_t e1, int lane, bool act, float (&acc)[4]) {
+    for (; e + 12 < e1; e += 16) {
+        float f[4][4];
+        int64_t j[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) j[q] = a.idx[e + 4 * q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (act) ld4f(F + j[q] * a.ld + 4 * lane, f[q]);
+            else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.f;
+        }
+        float d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            d[q] = uu[0] * f[q][0];
+#pragma unroll
+            for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float er = a.val[e + 4 * q] - d[q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(er, f[q][i], acc[i]);
+        }
+    }
+    for (; e < e1; e += 4) {
+        const int64_t j0 = a.idx[e];
+        float f0[4] = {0.f, 0.f, 0.f, 0.f};
+        if (act) ld4f(F + j0 * a.ld + 4 * lane, f0);
+        float d0 = uu[0] * f0[0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) d0 = fmaf(uu[i], f0[i], d0);
+        d0 = wsum(d0);
+        const float e0 = a.val[e] - d0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = fmaf(e0, f0[i], acc[i]);
+    }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -110,8 +159,16 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
         float *gb = a.Gbar ? reinterpret_cast<float *>(a.Gbar) + row * a.ld : nullptr;
         const float lam_n = (float)(a.lambda * (double)n);
         bool ok = n > 0;
+        // current row u0 = x_i (fold-in: 0), one 4-wide slot per lane
+        const bool act = 4 * lane < a.ld;
+        float uu[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) uu[i] = (xi && 4 * lane + i < nf) ? xi[4 * lane + i] : 0.0f;
+        for (int k = t; k < nf; k += TC_THREADS) u[k] = xi ? xi[k] : 0.0f;
         if (ok) {
-            // ---- 1-2. gather + tensor-core Gram -------------------------------
+            // ---- 1-2. gather + tensor-core Gram, with the first FP32 residual
+            //      r0 = sum_e f_e (r_e - f_e . u0) of the chunk's ratings computed
+            //      while the chunk's copies and MMAs are in flight -------------
             const int nch = (n + KCH - 1) / KCH;
             int pend[2] = {0, 0};
             auto gather = [&](int ch, int st) {
@@ -144,10 +201,14 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                         pend[sn] = 0;
                     }
                     gather(ch + 1, sn);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
                 }
+                {
+                    const int64_t c0 = beg + (int64_t)ch * KCH;
+                    const int64_t c1 = (beg + n < c0 + KCH) ? beg + n : c0 + KCH;
+                    resid_range(a, F, uu, c0 + warp, c1, lane, act, acc);
+                }
+                if (ch + 1 < nch) cp_async_wait<1>();
+                else cp_async_wait<0>();
                 fence_proxy_async_smem();
                 __syncthreads();
                 if (t == 0) {
@@ -174,6 +235,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                 }
             }
             if (bail) break;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i];
             tc_fence_after();
             // ---- 3. TMEM -> FP32 A (row m of D is TMEM lane m) -----------------
             {
@@ -192,70 +255,33 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             }
             tc_fence_before();
             __syncthreads();
-            // symmetric part of D, lower triangle, plus lambda n I
+            // symmetric part of D, lower triangle, plus lambda n I; the first
+            // residual v1 = r0 - lambda n u0 (fixed order over the warps)
             if (t < nf) {
                 for (int c = 0; c < t; ++c) A[t * ldA + c] = 0.5f * (A[t * ldA + c] + A[c * ldA + t]);
                 A[t * ldA + t] += lam_n;
+                v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
             }
             __syncthreads();
-            // ---- 4. Cholesky, refinement from the current row ------------------
+            // ---- 4. Cholesky (inverted diagonal blocks), refinement ------------
             ok = chol_blocked128(A, ldA, nf, diag, work, t);
+            if (ok) invert_diag_blocks128(A, ldA, nf, diag, t);
             if (!ok && t == 0) atomicAdd(a.notspd, 1);
         }
         if (ok) {
-            for (int k = t; k < nf; k += TC_THREADS) u[k] = xi ? xi[k] : 0.0f;
-            for (int s = 0; s < a.refine; ++s) {
+            trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
+            for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
+            for (int s = 1; s < a.refine; ++s) {
                 __syncthreads();
-                float uu[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+                float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) uu[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
-                const bool act = 4 * lane < a.ld;
-                int64_t e = beg + warp;
-                for (; e + 12 < beg + n; e += 16) {
-                    float f[4][4];
-                    int64_t j[4];
+                for (int i = 0; i < 4; ++i) uk[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
+                resid_range(a, F, uk, beg + warp, beg + n, lane, act, ak);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) j[q] = a.idx[e + 4 * q];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (act) ld4f(F + j[q] * a.ld + 4 * lane, f[q]);
-                        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.f;
-                    }
-                    float d[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        d[q] = uu[0] * f[q][0];
-#pragma unroll
-                        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float er = a.val[e + 4 * q] - d[q];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) acc[i] = fmaf(er, f[q][i], acc[i]);
-                    }
-                }
-                for (; e < beg + n; e += 4) {
-                    const int64_t j0 = a.idx[e];
-                    float f0[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (act) ld4f(F + j0 * a.ld + 4 * lane, f0);
-                    float d0 = uu[0] * f0[0];
-#pragma unroll
-                    for (int i = 1; i < 4; ++i) d0 = fmaf(uu[i], f0[i], d0);
-                    d0 = wsum(d0);
-                    const float e0 = a.val[e] - d0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[i] = fmaf(e0, f0[i], acc[i]);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i];
+                for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = ak[i];
                 __syncthreads();
                 if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
-                trisolve_blocked128(A, ldA, nf, diag, v1, v2, colk, t);
+                trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
                 for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             }
         } else {
