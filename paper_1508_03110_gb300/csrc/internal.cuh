@@ -94,6 +94,23 @@ struct als_ctx {
 
 #define RED_MAXB 512
 
+// Compensated (Kahan) accumulation s += x with the lost low part kept in c
+// (the sum is s - c).  Used for the FP32 sums over a row's ratings, which run
+// to tens of thousands of terms; for double it is a plain add (FP64 issue is
+// scarce on this GPU and its rounding is already far below what the FP64
+// form needs).
+template <typename T>
+__device__ __forceinline__ void kadd(T &s, T &c, T x) {
+    if constexpr (sizeof(T) == 4) {
+        const T y = x - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    } else {
+        s += x;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // error reporting
 void als_set_error(const std::string &msg);

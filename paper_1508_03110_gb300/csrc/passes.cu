@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR; r < a.nrows; r += ngroups) {
         const int64_t row = a.order[a.row_begin + r];
         const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
-        T x[4], acc[4];
+        T x[4], acc[4], cmp[4];
         zero4(acc);
+        zero4(cmp);
         if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
         int64_t e = 0;
         for (; e + 2 <= n; e += 2) {
@@ -145,7 +146,10 @@ __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
             T d1 = gsum<LPR>(dot4(x, f1), mask);
             const T e0 = (T)a.val[beg + e] - d0, e1 = (T)a.val[beg + e + 1] - d1;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fma(e1, f1[i], fma(e0, f0[i], acc[i]));
+            for (int i = 0; i < 4; ++i) {
+                kadd(acc[i], cmp[i], e0 * f0[i]);
+                kadd(acc[i], cmp[i], e1 * f1[i]);
+            }
         }
         for (; e < n; ++e) {
             const int64_t j0 = a.idx[beg + e];
@@ -154,8 +158,10 @@ __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
             const T d0 = gsum<LPR>(dot4(x, f0), mask);
             const T e0 = (T)a.val[beg + e] - d0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fma(e0, f0[i], acc[i]);
+            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], e0 * f0[i]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] -= cmp[i];
         grad_finish<T, LPR>(a, row, n, gl, mask, x, acc);
     }
 }
@@ -175,8 +181,9 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
         const int64_t beg = a.ptr[row], n = a.ptr[row + 1] - beg;
         const int64_t seg = (n + NG - 1) / NG;
         const int64_t e0 = beg + gi * seg, e1 = min(beg + n, e0 + seg);
-        T x[4], acc[4];
+        T x[4], acc[4], cmp[4];
         zero4(acc);
+        zero4(cmp);
         if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
         for (int64_t e = e0; e < e1; ++e) {
             const int64_t j = a.idx[e];
@@ -185,10 +192,10 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
             const T d = gsum<LPR>(dot4(x, f), mask);
             const T er = (T)a.val[e] - d;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fma(er, f[i], acc[i]);
+            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[i]);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) part[gi][gl][i] = acc[i];
+        for (int i = 0; i < 4; ++i) part[gi][gl][i] = acc[i] - cmp[i];
         __syncthreads();
         if (gi == 0) {
             T tot[4];

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
                 for (int k = t; k < nf; k += TPR) u[k] = xi ? xi[k] : T(0);
                 for (int s = 0; s < a.refine; ++s) {
                     // res = sum_e f_e (r_e - f_e . u) - lambda n u
-                    T rv = T(0);
+                    T rv = T(0), rcmp = T(0);
                     for (int c0 = 0; c0 < n; c0 += CH) {
                         const int cn = min(CH, n - c0);
                         sw_gsync<TPR>();
@@ -150,10 +150,10 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
                         }
                         sw_gsync<TPR>();
                         if (t < nf)
-                            for (int c = 0; c < cn; ++c) rv = fma(err[c], Fc[c * ldA + t], rv);
+                            for (int c = 0; c < cn; ++c) kadd(rv, rcmp, err[c] * Fc[c * ldA + t]);
                     }
                     sw_gsync<TPR>();
-                    if (t < nf) v1[t] = rv - lam_n * u[t];
+                    if (t < nf) v1[t] = (rv - rcmp) - lam_n * u[t];
                     sw_trisolve<T, TPR>(A, ldA, nf, diag, v1, v2, colk, t);
                     for (int k = t; k < nf; k += TPR) u[k] += colk[k];
                     sw_gsync<TPR>();

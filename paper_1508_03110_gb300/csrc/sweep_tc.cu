@@ -74,7 +74,8 @@ __device__ __forceinline__ float wsum(float x) {
 // FP32 residual of the row's normal equations, one warp, lane = 4-wide slot;
 // four gathered rows in flight at a time.
 __device__ __forceinline__ void resid_range(const SweepArgs &a, const float *F, const float (&uu)[4], int64_t e,
-                                            int64_t e1, int lane, bool act, float (&acc)[4]) {
+                                            int64_t e1, int lane, bool act, float (&acc)[4],
+                                            float (&cmp)[4]) {
     for (; e + 12 < e1; e += 16) {
         float f[4][4];
         int64_t j[4];
@@ -100,7 +101,7 @@ __device__ __forceinline__ void resid_range(const SweepArgs &a, const float *F, 
         for (int q = 0; q < 4; ++q) {
             const float er = a.val[e + 4 * q] - d[q];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(er, f[q][i], acc[i]);
+            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
         }
     }
     for (; e < e1; e += 4) {
@@ -113,7 +114,7 @@ __device__ __forceinline__ void resid_range(const SweepArgs &a, const float *F, 
         d0 = wsum(d0);
         const float e0 = a.val[e] - d0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] = fmaf(e0, f0[i], acc[i]);
+        for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], e0 * f0[i]);
     }
 }
 
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
         bool ok = n > 0;
         // current row u0 = x_i (fold-in: 0), one 4-wide slot per lane
         const bool act = 4 * lane < a.ld;
-        float uu[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float uu[4], acc[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < 4; ++i) uu[i] = (xi && 4 * lane + i < nf) ? xi[4 * lane + i] : 0.0f;
         for (int k = t; k < nf; k += TC_THREADS) u[k] = xi ? xi[k] : 0.0f;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                 {
                     const int64_t c0 = beg + (int64_t)ch * KCH;
                     const int64_t c1 = (beg + n < c0 + KCH) ? beg + n : c0 + KCH;
-                    resid_range(a, F, uu, c0 + warp, c1, lane, act, acc);
+                    resid_range(a, F, uu, c0 + warp, c1, lane, act, acc, cmp);
                 }
                 if (ch + 1 < nch) cp_async_wait<1>();
                 else cp_async_wait<0>();
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             }
             if (bail) break;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i];
+            for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i] - cmp[i];
             tc_fence_after();
             // ---- 3. TMEM -> FP32 A (row m of D is TMEM lane m) -----------------
             {
@@ -273,12 +274,12 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             for (int s = 1; s < a.refine; ++s) {
                 __syncthreads();
-                float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f};
+                float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) uk[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
-                resid_range(a, F, uk, beg + warp, beg + n, lane, act, ak);
+                resid_range(a, F, uk, beg + warp, beg + n, lane, act, ak, ck);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = ak[i];
+                for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = ak[i] - ck[i];
                 __syncthreads();
                 if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
                 trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
