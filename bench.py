@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving"])
+    ap.add_argument("--rates", default="1e3,1e4,1e5", help="serving: Poisson arrival rates (req/s)")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--jobs", type=int, default=2, help="serving: factorisation jobs per rate")
     ap.add_argument("--tol", type=float, default=1e-6, help="s_to_tol: relative |g| tolerance")
     ap.add_argument("--budget", type=float, default=300.0, help="s_to_tol: seconds per method")
     return ap.parse_args()
@@ -128,6 +131,85 @@ def run_s_to_tol(args):
                                 "trajectory": traj[:: max(1, len(traj) // 40)]}
         print(json.dumps({name: out["methods"][name]["reached"], "final": out["methods"][name]["final"]}),
               file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """Fold-in serving against a fixed M of 26,744 items x n_f = 100: Poisson
+    arrivals at each rate for `duration` seconds, request degree log-uniform in
+    [1, 5000] with Zipf items and half-star values, while `jobs` ALS-NCG
+    factorisation jobs (n_f = 20, ratings log-uniform in [1e5, 5e6]) are
+    admitted and run in between.  Latency is submit-to-result on the host."""
+    import random
+    import threading
+
+    import torch
+    import synth
+    from paper_1508_03110_gb300 import ALS, Server
+
+    n_m, n_f, lam = 26_744, 100, 0.05
+    pool_n = 4096
+    ptr, items, vals = synth.foldin_requests(pool_n, n_m, 1, 5000, seed=5)
+    pool = [(np.ascontiguousarray(items[ptr[q]:ptr[q + 1]]), np.ascontiguousarray(vals[ptr[q]:ptr[q + 1]]))
+            for q in range(pool_n)]
+    # a small ratings set that touches every item only serves to create the
+    # model context; M itself is set directly
+    mp, mi, mv = synth.foldin_requests(64, n_m, 500, 5000, seed=6)
+    mrows = np.repeat(np.arange(64, dtype=np.int32), np.diff(mp))
+    jobs = synth.make_batch(max(1, args.jobs), 100_000, 5_000_000, 0.001, 0.05, seed=5)
+    rates = [float(x) for x in args.rates.split(",")]
+    out = {"mode": "serving", "workload": f"fold-in against M {n_m:,} x {n_f} (synthetic), request degree "
+           f"log-uniform [1, 5000], Poisson arrivals; {len(jobs)} interleaved ALS-NCG jobs n_f=20 "
+           f"(ratings {[len(j[4]) for j in jobs]})", "results": []}
+    for prec in ("mixed", "fp64"):
+        model = ALS(64, n_m, mrows, mi, mv, n_f, lam, precision=prec)
+        model.set_factors(np.zeros((64, n_f)), synth.init_factors(0, n_m, n_f, 7).reshape(n_m, n_f))
+        torch.cuda.synchronize()
+        for rate in rates:
+            n_req = max(1, int(rate * args.duration))
+            rng = random.Random(int(rate))
+            srv = Server(model, max_batch=256, slots=4, max_jobs=2)
+            tickets = []
+            lat = []
+            stop = threading.Event()
+
+            def collector():
+                i = 0
+                while i < n_req:
+                    if i < len(tickets):
+                        lat.append(srv.wait(tickets[i], timeout=120.0)[1])
+                        i += 1
+                    elif stop.is_set():
+                        break
+                    else:
+                        time.sleep(1e-4)
+            th = threading.Thread(target=collector)
+            th.start()
+            jt = [srv.submit_job(j[0], j[1], j[2], j[3], j[4], synth.init_factors(j[0], j[1], 20, 9 + q), 20,
+                                 20, lam, precision=prec) for q, j in enumerate(jobs)]
+            t0 = time.perf_counter()
+            t_next = t0
+            for q in range(n_req):
+                t_next += rng.expovariate(rate)
+                while time.perf_counter() < t_next:
+                    pass
+                tickets.append(srv.submit_foldin(*pool[q % pool_n]))
+            t_sub = time.perf_counter() - t0
+            th.join()
+            t_all = time.perf_counter() - t0
+            stop.set()
+            job_lat = [srv.wait(t, timeout=600.0)[1] for t in jt]
+            st = srv.stats()
+            srv.close()
+            lat_ms = np.sort(np.array(lat)) * 1e3
+            res = {"precision": prec, "rate_offered": rate, "requests": n_req,
+                   "rate_submitted": n_req / t_sub, "rate_served": n_req / t_all,
+                   "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                   "max_ms": float(lat_ms[-1]), "server_p50_ms": st["p50_s"] * 1e3,
+                   "server_p99_ms": st["p99_s"] * 1e3, "job_latency_s": job_lat}
+            out["results"].append(res)
+            print(json.dumps(res), file=sys.stderr, flush=True)
+        model.close()
     print(json.dumps(out), flush=True)
 
 
@@ -275,6 +357,9 @@ def main():
         return
     if args.mode == "s_to_tol":
         run_s_to_tol(args)
+        return
+    if args.mode == "serving":
+        run_serving(args)
         return
     import torch
     import synth

@@ -135,6 +135,28 @@ ALS_API als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m, i
                       const int32_t *cols, const float *vals, int on_device,
                       void *cuda_stream, als_ctx **out);
 
+/* Many independent factorisation problems in one context (batched jobs; the
+ * paper solves one problem at a time).  Problem q has n_u[q] users, n_m[q]
+ * items and nnz[q] ratings; rows/cols/vals hold the problems' COO triplets one
+ * after the other (sum of nnz entries), with ids local to each problem.  All
+ * problems share cfg (n_f, lambda, precision, ...).  The device stores them as
+ * one block-diagonal problem (users of problem q at offset sum_{p<q} n_u[p],
+ * likewise items), so every sweep and rating pass covers all problems in the
+ * same launches; the line search (Algorithm 3), beta-bar (Eq. 8), the
+ * fallback and the stopping test are per problem.  Factors and vectors use
+ * the global layout: all problems' U rows, then all problems' M rows.
+ * alsncg_run stops when every problem meets the tolerance; als_loss /
+ * als_grad / als_linesearch_coeffs return sums over the problems; the state
+ * calls are not supported for batched contexts (ALS_ENOTSUP). */
+ALS_API als_status als_create_batched(const als_config *cfg, int32_t n_prob, const int64_t *n_u,
+                                      const int64_t *n_m, const int64_t *nnz, const int32_t *rows,
+                                      const int32_t *cols, const float *vals, int on_device,
+                                      void *cuda_stream, als_ctx **out);
+
+/* Per-problem record of the last Algorithm 2 iteration of a batched context:
+ * out[q] for q < n_prob (n_prob = 1 for an ordinary context).  Synchronous. */
+ALS_API als_status als_batch_info(als_ctx *ctx, int32_t n_prob, als_iter_info *out);
+
 /* Inspection of what the device builder made (§V-B storage), copied to host
  * arrays; any pointer may be NULL.  uptr[n_u+1] / uidx[nnz] / uval[nnz]: by
  * user, items ascending; mptr[n_m+1] / midx[nnz] / mval[nnz]: by item, users
@@ -230,6 +252,69 @@ ALS_API als_status als_linesearch_coeffs_static(int64_t n_u, int64_t n_m, int32_
 ALS_API als_status als_foldin(als_ctx *ctx, int64_t n_req, const int64_t *req_ptr,
                       const int32_t *items, const float *vals, int on_device_in,
                       void *u_out, int dtype, int on_device_out);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of fold-in requests and small factorisation
+ * jobs (the paper has no serving layer; fold-in is Eq. (3) for new users).
+ * A server owns one worker thread and its own CUDA streams.  Fold-in
+ * requests (a new user's items and ratings) are answered against the model
+ * context's current M: pending requests are packed into device batches as
+ * they arrive (up to max_batch requests / max_batch_ratings ratings per
+ * batch, `slots` batches in flight), so requests that arrive while earlier
+ * batches run are admitted as soon as a batch slot frees.  Jobs (whole
+ * ALS-NCG problems) are admitted while their estimated device memory fits
+ * hbm_budget_bytes and fewer than max_jobs run; each runs on its own context
+ * and stream, one iteration at a time, interleaved with the fold-in batches.
+ * Every result is computed exactly as it would be alone: rows and jobs are
+ * independent, so batching changes timing only.  While a server exists the
+ * model context must not be used by other calls.  All server calls are
+ * thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct als_server als_server;
+
+typedef struct {
+    int32_t max_batch;           /* fold-in requests per device batch (256)        */
+    int64_t max_batch_ratings;   /* ratings per device batch (1 << 20)             */
+    int32_t slots;               /* fold-in batches in flight (4)                  */
+    int32_t max_jobs;            /* factorisation jobs running at once (4)         */
+    size_t hbm_budget_bytes;     /* device memory for jobs (0 = no limit)          */
+} als_server_config;
+
+ALS_API void als_server_config_default(als_server_config *cfg);
+
+/* Start a server answering fold-in requests against model's M. */
+ALS_API als_status als_server_create(als_ctx *model, const als_server_config *cfg, als_server **out);
+
+/* Enqueue a fold-in request: n ratings (items[n] < n_m of the model, finite
+ * vals[n]); copies the arrays.  *ticket identifies it. */
+ALS_API als_status als_server_submit_foldin(als_server *srv, int64_t n, const int32_t *items,
+                                            const float *vals, int64_t *ticket);
+
+/* Enqueue a factorisation job: COO ratings (host), x0 = n_u + n_m rows of
+ * cfg->n_f doubles (host), run `iters` ALS-NCG iterations.  Copies inputs.
+ * ALS_EBUDGET if the job alone exceeds the server's budget. */
+ALS_API als_status als_server_submit_job(als_server *srv, const als_config *cfg, int64_t n_u,
+                                         int64_t n_m, int64_t nnz, const int32_t *rows,
+                                         const int32_t *cols, const float *vals, const double *x0,
+                                         int32_t iters, int64_t *ticket);
+
+/* Wait up to timeout_s seconds for a ticket.  Fold-in: result[n_f] floats
+ * (u); job: result[(n_u + n_m) * n_f] doubles (x after the iterations).
+ * *latency_s = submit-to-completion time.  ALS_ETIMEOUT if not done yet (the
+ * ticket stays valid); once the work has finished, successfully or not, the
+ * call releases the ticket.  A failed batch or job returns its error
+ * (ALS_ECUDA, ALS_ETIMEOUT for an expired bounded device wait, ...). */
+ALS_API als_status als_server_wait(als_server *srv, int64_t ticket, double timeout_s, void *result,
+                                   double *latency_s);
+
+/* Latency percentiles (seconds) and throughput (requests / s between the
+ * first submission and the last completion) of the completed fold-in
+ * requests so far. */
+ALS_API als_status als_server_stats(als_server *srv, double *p50_s, double *p99_s,
+                                    int64_t *completed, double *requests_per_s);
+
+/* Stop the worker after the queued work finishes and release everything. */
+ALS_API void als_server_destroy(als_server *srv);
 
 /* Wait for all work enqueued by this context. */
 ALS_API als_status als_sync(als_ctx *ctx);

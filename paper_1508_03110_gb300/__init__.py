@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import (ALS_FP64, ALS_MIXED, ALS_LS_BACKTRACK, ALS_LS_EXACT, ALS_DT_F64, ALS_DT_F32,  # noqa: F401
                    ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC, ALSError, IterInfo)
 
-__all__ = ["ALS", "ALSError", "load", "info_dict"]
+__all__ = ["ALS", "ALSBatch", "Server", "ALSError", "load", "info_dict", "make_config"]
 
 
 def load():
@@ -52,6 +52,23 @@ class _Buf:
             self.on_device = 0
 
 
+def make_config(n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=1, gram_path="auto",
+                hbm_budget_bytes=0, ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
+    """An als_config with the library defaults and the given fields."""
+    cfg = _lib.Config()
+    _lib.load().als_config_default(ctypes.byref(cfg))
+    cfg.n_f = int(n_f)
+    cfg.lam = float(lam)
+    cfg.precision = {"fp64": ALS_FP64, "mixed": ALS_MIXED}[precision]
+    cfg.ls_mode = {"backtrack": ALS_LS_BACKTRACK, "exact": ALS_LS_EXACT}[ls_mode]
+    cfg.ls_alpha0, cfg.ls_tau, cfg.ls_c = float(ls_alpha0), float(ls_tau), float(ls_c)
+    cfg.ls_max_shrinks = int(ls_max_shrinks)
+    cfg.refine_steps = int(refine_steps)
+    cfg.gram_path = {"auto": ALS_GRAM_AUTO, "fma": ALS_GRAM_FMA, "tc": ALS_GRAM_TC}[gram_path]
+    cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+    return cfg
+
+
 class ALS:
     """One factorisation problem R ~ U^T M on the current CUDA device.
 
@@ -65,17 +82,8 @@ class ALS:
         torch = _torch()
         self.lib = _lib.load()
         self.n_u, self.n_m, self.n_f = int(n_u), int(n_m), int(n_f)
-        cfg = _lib.Config()
-        self.lib.als_config_default(ctypes.byref(cfg))
-        cfg.n_f = self.n_f
-        cfg.lam = float(lam)
-        cfg.precision = {"fp64": ALS_FP64, "mixed": ALS_MIXED}[precision]
-        cfg.ls_mode = {"backtrack": ALS_LS_BACKTRACK, "exact": ALS_LS_EXACT}[ls_mode]
-        cfg.ls_alpha0, cfg.ls_tau, cfg.ls_c = float(ls_alpha0), float(ls_tau), float(ls_c)
-        cfg.ls_max_shrinks = int(ls_max_shrinks)
-        cfg.refine_steps = int(refine_steps)
-        cfg.gram_path = {"auto": ALS_GRAM_AUTO, "fma": ALS_GRAM_FMA, "tc": ALS_GRAM_TC}[gram_path]
-        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg = make_config(self.n_f, lam, precision, ls_mode, refine_steps, gram_path, hbm_budget_bytes,
+                          ls_alpha0, ls_tau, ls_c, ls_max_shrinks)
         # device memory comes from torch's caching allocator
         self._blocks = {}
 
@@ -257,3 +265,157 @@ class ALS:
 
     def sync(self):
         _lib.check(self.lib.als_sync(self.ctx), "als_sync")
+
+
+class ALSBatch(ALS):
+    """Many independent problems (list of (n_u, n_m, rows, cols, vals) with
+    local ids) sharing n_f, lambda and precision, solved in the same launches.
+    Vectors use the global layout: every problem's U rows, then every
+    problem's M rows."""
+
+    def __init__(self, problems, n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=1,
+                 gram_path="auto", hbm_budget_bytes=0, stream=None):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.n_prob = len(problems)
+        self.sizes = [(int(p[0]), int(p[1])) for p in problems]
+        self.n_u = sum(s[0] for s in self.sizes)
+        self.n_m = sum(s[1] for s in self.sizes)
+        self.n_f = int(n_f)
+        cfg = make_config(self.n_f, lam, precision, ls_mode, refine_steps, gram_path, hbm_budget_bytes)
+
+        def _alloc(nbytes, stream_, user):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream_ or 0)
+
+        def _free(ptr, nbytes, stream_, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = _lib.ALLOC_FN(_alloc)
+        self._free_cb = _lib.FREE_FN(_free)
+        cfg.alloc, cfg.free = self._alloc_cb, self._free_cb
+        self.cfg = cfg
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nu = np.array([s[0] for s in self.sizes], np.int64)
+        nm = np.array([s[1] for s in self.sizes], np.int64)
+        nz = np.array([len(p[3]) for p in problems], np.int64)
+        rows = np.ascontiguousarray(np.concatenate([np.asarray(p[2], np.int32) for p in problems]), np.int32)
+        cols = np.ascontiguousarray(np.concatenate([np.asarray(p[3], np.int32) for p in problems]), np.int32)
+        vals = np.ascontiguousarray(np.concatenate([np.asarray(p[4], np.float32) for p in problems]), np.float32)
+        self.nnz = int(nz.sum())
+        ctx = ctypes.c_void_p()
+        st = self.lib.als_create_batched(ctypes.byref(cfg), self.n_prob, nu.ctypes.data, nm.ctypes.data,
+                                         nz.ctypes.data, rows.ctypes.data, cols.ctypes.data, vals.ctypes.data,
+                                         0, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        _lib.check(st, "als_create_batched")
+        self.ctx = ctx
+        self._uoff = np.concatenate([[0], np.cumsum(nu)])
+        self._moff = np.concatenate([[0], np.cumsum(nm)])
+
+    def join_x(self, xs):
+        """Global x from per-problem x vectors (Eq. 5 layout each)."""
+        us, ms = [], []
+        for (nu, nm), x in zip(self.sizes, xs):
+            x = np.asarray(x, np.float64).reshape(nu + nm, self.n_f)
+            us.append(x[:nu]); ms.append(x[nu:])
+        return np.concatenate(us + ms).reshape(-1)
+
+    def split_x(self, x):
+        x = np.asarray(x).reshape(self.n_u + self.n_m, self.n_f)
+        out = []
+        for q in range(self.n_prob):
+            U = x[self._uoff[q]:self._uoff[q + 1]]
+            M = x[self.n_u + self._moff[q]:self.n_u + self._moff[q + 1]]
+            out.append(np.concatenate([U.reshape(-1), M.reshape(-1)]))
+        return out
+
+    def infos(self):
+        arr = (IterInfo * self.n_prob)()
+        _lib.check(self.lib.als_batch_info(self.ctx, self.n_prob, arr), "als_batch_info")
+        return [info_dict(a) for a in arr]
+
+
+class Server:
+    """Continuous-batching server over a model's M (als_server_* in the C ABI).
+
+    Fold-in requests (one new user's items and ratings) are packed into device
+    batches by the library's worker thread as they arrive; factorisation jobs
+    are admitted by device-memory budget and advanced one ALS-NCG iteration at
+    a time between the batches.  The model must not be used by other calls
+    while the server exists.
+    """
+
+    def __init__(self, model, max_batch=256, max_batch_ratings=1 << 20, slots=4, max_jobs=4,
+                 hbm_budget_bytes=0):
+        self.lib = _lib.load()
+        self.model = model
+        cfg = _lib.ServerConfig()
+        self.lib.als_server_config_default(ctypes.byref(cfg))
+        cfg.max_batch, cfg.max_batch_ratings, cfg.slots = int(max_batch), int(max_batch_ratings), int(slots)
+        cfg.max_jobs, cfg.hbm_budget_bytes = int(max_jobs), int(hbm_budget_bytes)
+        srv = ctypes.c_void_p()
+        _lib.check(self.lib.als_server_create(model.ctx, ctypes.byref(cfg), ctypes.byref(srv)),
+                   "als_server_create")
+        self.srv = srv
+        self._kind = {}   # ticket -> result shape
+
+    def close(self):
+        if getattr(self, "srv", None):
+            self.lib.als_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit_foldin(self, items, vals):
+        items = np.ascontiguousarray(items, np.int32)
+        vals = np.ascontiguousarray(vals, np.float32)
+        if items.shape != vals.shape:
+            raise ValueError("items and vals must have the same length")
+        t = ctypes.c_int64()
+        _lib.check(self.lib.als_server_submit_foldin(self.srv, len(items), items.ctypes.data, vals.ctypes.data,
+                                                     ctypes.byref(t)), "als_server_submit_foldin")
+        self._kind[t.value] = ("foldin", (self.model.n_f,), np.float32)
+        return t.value
+
+    def submit_job(self, n_u, n_m, rows, cols, vals, x0, iters, n_f, lam, **config):
+        """x0: (n_u + n_m) x n_f float64 initial factors; config: make_config's keywords."""
+        cfg = make_config(n_f, lam, **config)
+        rows = np.ascontiguousarray(rows, np.int32)
+        cols = np.ascontiguousarray(cols, np.int32)
+        vals = np.ascontiguousarray(vals, np.float32)
+        x0 = np.ascontiguousarray(x0, np.float64).reshape(int(n_u) + int(n_m), int(n_f))
+        t = ctypes.c_int64()
+        _lib.check(self.lib.als_server_submit_job(self.srv, ctypes.byref(cfg), int(n_u), int(n_m), len(vals),
+                                                  rows.ctypes.data, cols.ctypes.data, vals.ctypes.data,
+                                                  x0.ctypes.data, int(iters), ctypes.byref(t)),
+                   "als_server_submit_job")
+        self._kind[t.value] = ("job", x0.shape, np.float64)
+        return t.value
+
+    def wait(self, ticket, timeout=60.0):
+        """(result, latency in seconds) of a ticket; raises ALSError (ALS_ETIMEOUT) if not done in time."""
+        _, shape, dt = self._kind[ticket]
+        out = np.empty(shape, dt)
+        lat = ctypes.c_double()
+        st = self.lib.als_server_wait(self.srv, ticket, float(timeout), out.ctypes.data, ctypes.byref(lat))
+        if st != _lib.ALS_ETIMEOUT:
+            del self._kind[ticket]
+        _lib.check(st, "als_server_wait")
+        return out, lat.value
+
+    def stats(self):
+        p50, p99, rps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _lib.check(self.lib.als_server_stats(self.srv, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n),
+                                             ctypes.byref(rps)), "als_server_stats")
+        return {"p50_s": p50.value, "p99_s": p99.value, "completed": n.value, "requests_per_s": rps.value}

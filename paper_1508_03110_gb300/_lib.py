@@ -43,12 +43,22 @@ class IterInfo(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("max_batch", ctypes.c_int32), ("max_batch_ratings", ctypes.c_int64), ("slots", ctypes.c_int32),
+        ("max_jobs", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+    ]
+
+
 # name -> (restype, argtypes); the full list of symbols include/als.h declares
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
     "als_config_default": (None, [ctypes.POINTER(Config)]),
     "als_create": (_i32, [ctypes.POINTER(Config), _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i32, _vp,
                           ctypes.POINTER(_vp)]),
+    "als_create_batched": (_i32, [ctypes.POINTER(Config), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp,
+                                  ctypes.POINTER(_vp)]),
+    "als_batch_info": (_i32, [_vp, _i32, ctypes.POINTER(IterInfo)]),
     "als_get_ratings": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "als_set_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "als_get_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
@@ -63,6 +73,15 @@ SIGNATURES = {
     "als_linesearch_coeffs_static": (_i32, [_i64, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
                                             _i32, _vp, _vp]),
     "als_foldin": (_i32, [_vp, _i64, _vp, _vp, _vp, _i32, _vp, _i32, _i32]),
+    "als_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
+    "als_server_create": (_i32, [_vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
+    "als_server_submit_foldin": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
+    "als_server_submit_job": (_i32, [_vp, ctypes.POINTER(Config), _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i32,
+                                     ctypes.POINTER(_i64)]),
+    "als_server_wait": (_i32, [_vp, _i64, _dbl, _vp, ctypes.POINTER(_dbl)]),
+    "als_server_stats": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_i64),
+                                ctypes.POINTER(_dbl)]),
+    "als_server_destroy": (None, [_vp]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
     "als_last_error": (ctypes.c_char_p, []),

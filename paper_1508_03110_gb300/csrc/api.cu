@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -25,6 +26,20 @@ static thread_local std::string g_err;
 void als_set_error(const std::string &msg) { g_err = msg; }
 
 extern "C" const char *als_last_error(void) { return g_err.c_str(); }
+
+als_status raise_smem_limit(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    ALS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{dev, func}];
+    if (bytes > cur) {
+        ALS_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        cur = bytes;
+    }
+    return ALS_OK;
+}
 
 extern "C" const char *als_version(void) { return "als-ncg-gb300 1.0 (sm_103a)"; }
 
@@ -186,7 +201,8 @@ als_status lscoef_into(als_ctx *c, void *X, void *P) {
 }
 
 als_status read_scalars(als_ctx *c) {
-    ALS_CUDA_TRY(cudaMemcpyAsync(c->hS, c->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->hS, c->S, (size_t)c->n_prob * S_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
     ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->hflags[7]) {
@@ -228,8 +244,26 @@ als_status ncg_iter(als_ctx *c, int gcur) {
     return launch_update_p(c);
 }
 
-void fill_info(const als_ctx *c, als_iter_info *o) {
-    const double *S = c->hS;
+// sum over the problems of a per-problem scalar slot (one problem: the slot)
+double sum_slot(const als_ctx *c, int slot) {
+    double s = 0.0;
+    for (int q = 0; q < c->n_prob; ++q) s += c->hS[(size_t)q * S_COUNT + slot];
+    return s;
+}
+
+// the worst problem's |g_k| / |g_0|
+double worst_rel_gnorm(const als_ctx *c) {
+    double w = 0.0;
+    for (int q = 0; q < c->n_prob; ++q) {
+        const double *S = c->hS + (size_t)q * S_COUNT;
+        const double r = S[S_GG0] > 0.0 ? std::sqrt(S[S_GG] / S[S_GG0]) : 0.0;
+        w = std::max(w, r);
+    }
+    return w;
+}
+
+void fill_info_q(const als_ctx *c, int q, als_iter_info *o) {
+    const double *S = c->hS + (size_t)q * S_COUNT;
     o->k = c->k;
     o->f = S[S_F];
     o->gnorm = std::sqrt(S[S_GG]);
@@ -244,6 +278,18 @@ void fill_info(const als_ctx *c, als_iter_info *o) {
     o->kernels = 0;
 }
 
+// one record for the whole context: problem 0, or for a batch the sums of f
+// and |g|^2 over the problems (alpha, beta, c: problem 0)
+void fill_info(const als_ctx *c, als_iter_info *o) {
+    fill_info_q(c, 0, o);
+    if (c->n_prob > 1) {
+        o->f = sum_slot(c, S_F);
+        o->gnorm = std::sqrt(sum_slot(c, S_GG));
+        o->gnorm0 = std::sqrt(sum_slot(c, S_GG0));
+        o->fallbacks = (int64_t)sum_slot(c, S_NFALL);
+    }
+}
+
 als_status loss_now(als_ctx *c, double *f) {
     als_status s = lscoef_into(c, c->X, nullptr);
     if (s != ALS_OK) return s;
@@ -251,7 +297,7 @@ als_status loss_now(als_ctx *c, double *f) {
     if (s != ALS_OK) return s;
     s = read_scalars(c);
     if (s != ALS_OK) return s;
-    *f = c->hS[S_RED];
+    *f = sum_slot(c, S_RED);
     return ALS_OK;
 }
 
@@ -316,10 +362,59 @@ extern "C" void als_config_default(als_config *cfg) {
     cfg->gram_path = ALS_GRAM_AUTO;
 }
 
+namespace {
+// batched problems: per-problem sizes (host) for create_impl
+struct BatchSpec {
+    int n_prob;
+    std::vector<int64_t> segu, segm, nnzoff;  // prefix sums, n_prob + 1 entries each
+};
+}  // namespace
+
+static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
+                              const int32_t *rows_or_null, const int64_t *rowptr_or_null, const int32_t *cols,
+                              const float *vals, int on_device, void *cuda_stream, als_ctx **out,
+                              const BatchSpec *bs);
+
 extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
                                  const int32_t *rows_or_null, const int64_t *rowptr_or_null,
                                  const int32_t *cols, const float *vals, int on_device, void *cuda_stream,
                                  als_ctx **out) {
+    return create_impl(cfg, n_u, n_m, nnz, rows_or_null, rowptr_or_null, cols, vals, on_device, cuda_stream, out,
+                       nullptr);
+}
+
+extern "C" als_status als_create_batched(const als_config *cfg, int32_t n_prob, const int64_t *n_u,
+                                         const int64_t *n_m, const int64_t *nnz, const int32_t *rows,
+                                         const int32_t *cols, const float *vals, int on_device, void *cuda_stream,
+                                         als_ctx **out) {
+    if (!out) { als_set_error("als_create_batched: out is NULL"); return ALS_EINVAL; }
+    *out = nullptr;
+    if (n_prob < 1 || n_prob > (1 << 20) || !n_u || !n_m || !nnz) {
+        als_set_error("als_create_batched: need 1 <= n_prob <= 2^20 and per-problem size arrays");
+        return ALS_EINVAL;
+    }
+    BatchSpec bs;
+    bs.n_prob = n_prob;
+    bs.segu.assign(1, 0);
+    bs.segm.assign(1, 0);
+    bs.nnzoff.assign(1, 0);
+    for (int q = 0; q < n_prob; ++q) {
+        if (n_u[q] < 1 || n_m[q] < 1 || nnz[q] < 0) {
+            als_set_error("als_create_batched: every problem needs n_u, n_m >= 1 and nnz >= 0");
+            return ALS_EINVAL;
+        }
+        bs.segu.push_back(bs.segu.back() + n_u[q]);
+        bs.segm.push_back(bs.segm.back() + n_m[q]);
+        bs.nnzoff.push_back(bs.nnzoff.back() + nnz[q]);
+    }
+    return create_impl(cfg, bs.segu.back(), bs.segm.back(), bs.nnzoff.back(), rows, nullptr, cols, vals, on_device,
+                       cuda_stream, out, &bs);
+}
+
+static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
+                              const int32_t *rows_or_null, const int64_t *rowptr_or_null, const int32_t *cols,
+                              const float *vals, int on_device, void *cuda_stream, als_ctx **out,
+                              const BatchSpec *bs) {
     if (!out) { als_set_error("als_create: out is NULL"); return ALS_EINVAL; }
     *out = nullptr;
     if (!cfg) { als_set_error("als_create: cfg is NULL"); return ALS_EINVAL; }
@@ -397,14 +492,22 @@ extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m
     ALLOC(c->rowterm, 5 * (size_t)nrows * sizeof(double));
     ALLOC(c->partial, 5 * RED_MAXB * sizeof(double));
     ALLOC(c->ticket, 256);
-    ALLOC(c->S, S_COUNT * sizeof(double));
+    c->n_prob = bs ? bs->n_prob : 1;
+    ALLOC(c->S, (size_t)c->n_prob * S_COUNT * sizeof(double));
     ALLOC(c->dflags, 16 * sizeof(int));
+    if (bs) {
+        ALLOC(c->segu, (bs->n_prob + 1) * sizeof(int64_t));
+        ALLOC(c->segm, (bs->n_prob + 1) * sizeof(int64_t));
+        ALLOC(c->rowprob, nrows * sizeof(int32_t));
+        c->h_segu = bs->segu;
+        c->h_segm = bs->segm;
+    }
     if (c->use_tc) {
         c->shadow_rows = std::max(n_u, n_m);
         ALLOC(c->shadow, (size_t)c->shadow_rows * 2 * ALS_TC_LD * sizeof(__nv_bfloat16));
     }
 #undef ALLOC
-    if (cudaMallocHost(&c->hS, S_COUNT * sizeof(double)) != cudaSuccess ||
+    if (cudaMallocHost(&c->hS, (size_t)c->n_prob * S_COUNT * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->hflags, 16 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         als_set_error("als_create: pinned host allocation failed");
@@ -414,14 +517,59 @@ extern "C" als_status als_create(const als_config *cfg, int64_t n_u, int64_t n_m
         if (cudaMemsetAsync(p, 0, vbytes, c->stream) != cudaSuccess) { cudaGetLastError(); als_set_error("als_create: memset failed"); return fail(ALS_ECUDA); }
     }
     if (cudaMemsetAsync(c->ticket, 0, 256, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->S, 0, S_COUNT * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->S, 0, (size_t)c->n_prob * S_COUNT * sizeof(double), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->rowterm, 0, 5 * (size_t)nrows * sizeof(double), c->stream) != cudaSuccess) {
         cudaGetLastError();
         als_set_error("als_create: memset failed");
         return fail(ALS_ECUDA);
     }
-    s = build_ratings(c, rows_or_null, rowptr_or_null, cols, vals, on_device);
+    if (bs) {
+        // batched: per-problem local ids -> global ids of the block-diagonal problem
+        int32_t *drows = nullptr, *dcols = nullptr;
+        float *dvals = nullptr;
+        int64_t *dnnz = nullptr;
+        auto tmp = [&](void **p, size_t b) { return ctx_alloc(c, p, b); };
+        if ((s = tmp((void **)&drows, std::max<int64_t>(nnz, 1) * sizeof(int32_t))) != ALS_OK) return fail(s);
+        if ((s = tmp((void **)&dcols, std::max<int64_t>(nnz, 1) * sizeof(int32_t))) != ALS_OK) return fail(s);
+        if ((s = tmp((void **)&dvals, std::max<int64_t>(nnz, 1) * sizeof(float))) != ALS_OK) return fail(s);
+        if ((s = tmp((void **)&dnnz, (bs->n_prob + 1) * sizeof(int64_t))) != ALS_OK) return fail(s);
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        bool okc = cudaMemcpyAsync(c->segu, bs->segu.data(), (bs->n_prob + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+                   cudaMemcpyAsync(c->segm, bs->segm.data(), (bs->n_prob + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+                   cudaMemcpyAsync(dnnz, bs->nnzoff.data(), (bs->n_prob + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+        if (okc && nnz > 0)
+            okc = cudaMemcpyAsync(drows, rows_or_null, nnz * sizeof(int32_t), kind, c->stream) == cudaSuccess &&
+                  cudaMemcpyAsync(dcols, cols, nnz * sizeof(int32_t), kind, c->stream) == cudaSuccess &&
+                  cudaMemcpyAsync(dvals, vals, nnz * sizeof(float), kind, c->stream) == cudaSuccess;
+        if (!okc) {
+            als_set_error(std::string("als_create_batched: copy failed: ") + cudaGetErrorString(cudaGetLastError()));
+            return fail(ALS_ECUDA);
+        }
+        if ((s = launch_offset_ids(c, dnnz, bs->n_prob, c->segu, c->segm, drows, dcols, nnz, c->dflags + 8)) != ALS_OK)
+            return fail(s);
+        if ((s = launch_rowprob(c)) != ALS_OK) return fail(s);
+        int bad = 0;
+        if (cudaMemcpyAsync(&bad, c->dflags + 8, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            als_set_error("als_create_batched: synchronisation failed");
+            return fail(ALS_ECUDA);
+        }
+        if (bad) {
+            als_set_error("als_create_batched: " + std::to_string(bad) + " ratings with a local id out of range");
+            return fail(ALS_EINVAL);
+        }
+        s = build_ratings(c, drows, nullptr, dcols, dvals, 1);
+        ctx_free(c, drows);
+        ctx_free(c, dcols);
+        ctx_free(c, dvals);
+        ctx_free(c, dnnz);
+    } else {
+        s = build_ratings(c, rows_or_null, rowptr_or_null, cols, vals, on_device);
+    }
     if (s != ALS_OK) return fail(s);
     if (cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return fail(ALS_ECUDA); }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -485,6 +633,7 @@ extern "C" als_status als_get_state(als_ctx *c, void *x, void *p, void *g, void 
                                     double scalars[4], int dtype, int on_device) {
     if (!c || !valid_dtype(dtype)) { als_set_error("als_get_state: bad argument"); return ALS_EINVAL; }
     if (!c->ncg_ready) { als_set_error("als_get_state: ALS-NCG has not started"); return ALS_EINVAL; }
+    if (c->n_prob > 1) { als_set_error("als_get_state: not supported for batched contexts"); return ALS_ENOTSUP; }
     const int64_t rows = c->n_u + c->n_m;
     const size_t bytes = (size_t)rows * c->nf * dtype_size(dtype);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -514,6 +663,7 @@ extern "C" als_status als_set_state(als_ctx *c, const void *x, const void *p, co
         als_set_error("als_set_state: bad argument");
         return ALS_EINVAL;
     }
+    if (c->n_prob > 1) { als_set_error("als_set_state: not supported for batched contexts"); return ALS_ENOTSUP; }
     const int64_t rows = c->n_u + c->n_m;
     const size_t bytes = (size_t)rows * c->nf * dtype_size(dtype);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -596,7 +746,7 @@ extern "C" als_status alsncg_run(als_ctx *c, int32_t max_iter, double rel_tol, i
         if (done % check_every == 0 || done == max_iter) {
             s = read_scalars(c);
             if (s != ALS_OK) return s;
-            converged = std::sqrt(c->hS[S_GG]) <= rel_tol * std::sqrt(c->hS[S_GG0]);
+            converged = worst_rel_gnorm(c) <= rel_tol;
         }
     }
     if (iters_done) *iters_done = done;
@@ -634,7 +784,7 @@ extern "C" als_status als_grad(als_ctx *c, void *g_out, int dtype, int on_device
     if (gnorm) {
         s = read_scalars(c);
         if (s != ALS_OK) return s;
-        *gnorm = std::sqrt(c->hS[S_RED]);
+        *gnorm = std::sqrt(sum_slot(c, S_RED));
     } else if (g_out && !on_device) {
         ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
@@ -663,7 +813,7 @@ extern "C" als_status als_linesearch_coeffs(als_ctx *c, const void *p, int dtype
     if (s != ALS_OK) return s;
     s = read_scalars(c);
     if (s != ALS_OK) return s;
-    for (int i = 0; i < 5; ++i) cf[i] = c->hS[S_RED + i];
+    for (int i = 0; i < 5; ++i) cf[i] = sum_slot(c, S_RED + i);
     return ALS_OK;
 }
 
@@ -742,6 +892,17 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     TRY(cudaStreamSynchronize(c->stream));
 #undef TRY
     cleanup();
+    return ALS_OK;
+}
+
+extern "C" als_status als_batch_info(als_ctx *c, int32_t n_prob, als_iter_info *out) {
+    if (!c || !out || n_prob != c->n_prob) {
+        als_set_error("als_batch_info: bad argument (n_prob must equal the context's problem count)");
+        return ALS_EINVAL;
+    }
+    als_status s = read_scalars(c);
+    if (s != ALS_OK) return s;
+    for (int q = 0; q < n_prob; ++q) fill_info_q(c, q, out + q);
     return ALS_OK;
 }
 

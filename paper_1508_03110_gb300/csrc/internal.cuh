@@ -90,6 +90,12 @@ struct als_ctx {
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};   // kernel nodes per captured iteration
+
+    // batched problems (n_prob > 1): block-diagonal layout, per-problem scalars
+    int n_prob = 1;
+    int64_t *segu = nullptr, *segm = nullptr;  // device [n_prob + 1] user / item offsets
+    int32_t *rowprob = nullptr;                // device [n_u + n_m] problem of each row
+    std::vector<int64_t> h_segu, h_segm;
 };
 
 #define RED_MAXB 512
@@ -123,6 +129,12 @@ void als_set_error(const std::string &msg);
         }                                                                               \
     } while (0)
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it: contexts driven from other threads (a
+// server's worker, say) may launch the same kernel with a larger size at the
+// same time, and a lowered limit would fail their launch.
+als_status raise_smem_limit(const void *func, size_t bytes);
+
 // allocation through the configured hooks, counted against the HBM budget
 als_status ctx_alloc(als_ctx *c, void **p, size_t bytes);
 void ctx_free(als_ctx *c, void *p);
@@ -150,9 +162,12 @@ struct SweepArgs {
     int refine;
     int *notspd;
     int *timeout;           // set when a bounded device wait expired
+    cudaStream_t stream = nullptr;  // launch stream (nullptr: the context's)
 };
 als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
-als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64);
+// BF16 hi/lo shadow of F (rows x ld) into dst (nullptr: the context's shadow)
+als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst = nullptr,
+                          cudaStream_t stream = nullptr);
 
 // ---------------------------------------------------------------------------
 // passes (passes.cu)
@@ -186,5 +201,9 @@ als_status launch_convert_in(als_ctx *c, void *dst, const void *src, int64_t row
                              int src_ld);
 als_status launch_convert_out(als_ctx *c, void *dst, const void *src, int64_t rows, int dst_dtype,
                               int dst_ld);
+// batched problems: local ids + per-problem offsets -> global ids (and checks)
+als_status launch_offset_ids(als_ctx *c, const int64_t *nnzoff, int n_prob, const int64_t *segu,
+                             const int64_t *segm, int32_t *rows, int32_t *cols, int64_t nnz, int *flag);
+als_status launch_rowprob(als_ctx *c);
 als_status launch_check_requests(als_ctx *c, const int64_t *ptr, int64_t nreq, const int32_t *idx,
                                  const float *val, int64_t total, int64_t bound, int *flag);

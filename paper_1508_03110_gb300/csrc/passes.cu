@@ -503,6 +503,28 @@ __device__ void post_lselect(double *S, const LsParams lp) {
     S[S_SHRINK] = (double)k;
 }
 
+// scalar step after a reduction, on one problem's scalars (one thread)
+__device__ void run_post(double *S, int s_off, int post, const LsParams &lp) {
+    if (post == POST_LSELECT) {
+        post_lselect(S, lp);
+    } else if (post == POST_BETA) {
+        const double gg = S[s_off], gbg = S[s_off + 1], gbd = S[s_off + 2];
+        const double sk = S[S_S];
+        S[S_BETA] = (S[S_MODE] == 0.0 && sk != 0.0) ? gbd / sk : 0.0;
+        S[S_S] = gbg;
+        S[S_GG] = gg;
+    } else if (post == POST_INIT) {
+        S[S_GG] = S[s_off];
+        S[S_GG0] = S[s_off];
+        S[S_S] = S[s_off + 1];
+        S[S_MODE] = 0.0;
+        S[S_BETA] = 0.0;
+        S[S_NFALL] = 0.0;
+        S[S_ALPHA] = 0.0;
+        S[S_SHRINK] = 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const double *__restrict__ rowterm, int64_t n,
                                                         int nterms, double *__restrict__ partial,
                                                         unsigned *__restrict__ ticket, double *__restrict__ S,
@@ -545,45 +567,60 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const double *__restrict
     }
     if (threadIdx.x == 0) {
         *ticket = 0u;
-        if (post == POST_LSELECT) {
-            post_lselect(S, lp);
-        } else if (post == POST_BETA) {
-            const double gg = S[s_off], gbg = S[s_off + 1], gbd = S[s_off + 2];
-            const double sk = S[S_S];
-            S[S_BETA] = (S[S_MODE] == 0.0 && sk != 0.0) ? gbd / sk : 0.0;
-            S[S_S] = gbg;
-            S[S_GG] = gg;
-        } else if (post == POST_INIT) {
-            S[S_GG] = S[s_off];
-            S[S_GG0] = S[s_off];
-            S[S_S] = S[s_off + 1];
-            S[S_MODE] = 0.0;
-            S[S_BETA] = 0.0;
-            S[S_NFALL] = 0.0;
-            S[S_ALPHA] = 0.0;
-            S[S_SHRINK] = 0.0;
-        }
+        run_post(S, s_off, post, lp);
     }
+}
+
+// Batched problems: block q reduces problem q's user rows [segu[q], segu[q+1])
+// and item rows [n_u + segm[q], n_u + segm[q+1]) in a fixed order, then runs
+// the post-operation on problem q's scalars S + q * S_COUNT.
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_seg(const double *__restrict__ rowterm, int64_t n, int nterms,
+                                                            const int64_t *__restrict__ segu,
+                                                            const int64_t *__restrict__ segm, int64_t n_u,
+                                                            double *__restrict__ S, int s_off, int post, LsParams lp) {
+    __shared__ double red[RED_THREADS];
+    const int q = blockIdx.x;
+    double *Sq = S + (size_t)q * S_COUNT;
+    const int64_t u0 = segu[q], u1 = segu[q + 1], m0 = n_u + segm[q], m1 = n_u + segm[q + 1];
+    for (int t = 0; t < nterms; ++t) {
+        double s = 0.0;
+        for (int64_t i = u0 + threadIdx.x; i < u1; i += RED_THREADS) s += rowterm[t * n + i];
+        for (int64_t i = m0 + threadIdx.x; i < m1; i += RED_THREADS) s += rowterm[t * n + i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) Sq[s_off + t] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) run_post(Sq, s_off, post, lp);
 }
 
 // ---------------------------------------------------------------------------
 // vectors
 // ---------------------------------------------------------------------------
+// rowprob == nullptr: one problem; otherwise the scalars of row i / ld's problem
 template <typename T>
 __global__ void k_update_x(T *__restrict__ X, const T *__restrict__ Xbar, const T *__restrict__ P,
-                           const double *__restrict__ S, int64_t n) {
-    const bool fallback = S[S_MODE] != 0.0;
-    const T al = (T)S[S_ALPHA];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+                           const double *__restrict__ S, const int32_t *__restrict__ rowprob, int ld, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *Sq = rowprob ? S + (size_t)rowprob[i / ld] * S_COUNT : S;
+        const bool fallback = Sq[S_MODE] != 0.0;
+        const T al = (T)Sq[S_ALPHA];
         X[i] = fallback ? Xbar[i] : fma(al, P[i], X[i]);
+    }
 }
 
 template <typename T>
 __global__ void k_update_p(T *__restrict__ P, const T *__restrict__ Gbar, const double *__restrict__ S,
-                           int64_t n) {
-    const T be = (T)S[S_BETA];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+                           const int32_t *__restrict__ rowprob, int ld, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *Sq = rowprob ? S + (size_t)rowprob[i / ld] * S_COUNT : S;
+        const T be = (T)Sq[S_BETA];
         P[i] = fma(be, P[i], -Gbar[i]);
+    }
 }
 
 template <typename T>
@@ -693,6 +730,12 @@ als_status launch_lscoef_reg(als_ctx *c, const PassArgs &a) {
 }
 
 als_status launch_reduce(als_ctx *c, int nterms, int64_t n, int s_off, int post, const LsParams &lp) {
+    if (c->n_prob > 1) {
+        k_reduce_seg<<<(unsigned)c->n_prob, RED_THREADS, 0, c->stream>>>(c->rowterm, n, nterms, c->segu, c->segm,
+                                                                         c->n_u, c->S, s_off, post, lp);
+        ALS_CUDA_TRY(cudaGetLastError());
+        return ALS_OK;
+    }
     const int64_t want = (n + 8191) / 8192;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, RED_MAXB));
     k_reduce<<<g, RED_THREADS, 0, c->stream>>>(c->rowterm, n, nterms, c->partial, c->ticket, c->S, s_off,
@@ -704,8 +747,8 @@ als_status launch_reduce(als_ctx *c, int nterms, int64_t n, int s_off, int post,
 als_status launch_update_x(als_ctx *c) {
     const int64_t n = (c->n_u + c->n_m) * c->ld;
     const unsigned g = grid_for(c, n, 256);
-    if (c->f64) k_update_x<double><<<g, 256, 0, c->stream>>>((double *)c->X, (const double *)c->Xbar, (const double *)c->P, c->S, n);
-    else k_update_x<float><<<g, 256, 0, c->stream>>>((float *)c->X, (const float *)c->Xbar, (const float *)c->P, c->S, n);
+    if (c->f64) k_update_x<double><<<g, 256, 0, c->stream>>>((double *)c->X, (const double *)c->Xbar, (const double *)c->P, c->S, c->rowprob, c->ld, n);
+    else k_update_x<float><<<g, 256, 0, c->stream>>>((float *)c->X, (const float *)c->Xbar, (const float *)c->P, c->S, c->rowprob, c->ld, n);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
@@ -713,8 +756,8 @@ als_status launch_update_x(als_ctx *c) {
 als_status launch_update_p(als_ctx *c) {
     const int64_t n = (c->n_u + c->n_m) * c->ld;
     const unsigned g = grid_for(c, n, 256);
-    if (c->f64) k_update_p<double><<<g, 256, 0, c->stream>>>((double *)c->P, (const double *)c->Gbar, c->S, n);
-    else k_update_p<float><<<g, 256, 0, c->stream>>>((float *)c->P, (const float *)c->Gbar, c->S, n);
+    if (c->f64) k_update_p<double><<<g, 256, 0, c->stream>>>((double *)c->P, (const double *)c->Gbar, c->S, c->rowprob, c->ld, n);
+    else k_update_p<float><<<g, 256, 0, c->stream>>>((float *)c->P, (const float *)c->Gbar, c->S, c->rowprob, c->ld, n);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
@@ -771,6 +814,64 @@ als_status launch_check_requests(als_ctx *c, const int64_t *ptr, int64_t nreq, c
     ALS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
     const unsigned g = grid_for(c, std::max(total, nreq), 256);
     k_check_requests<<<g, 256, 0, c->stream>>>(ptr, nreq, idx, val, total, bound, flag);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched problems: global ids and the row -> problem map
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_offset_ids(const int64_t *__restrict__ nnzoff, int n_prob, const int64_t *__restrict__ segu,
+                             const int64_t *__restrict__ segm, int32_t *__restrict__ rows, int32_t *__restrict__ cols,
+                             int64_t nnz, int *__restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int lo = 0, hi = n_prob;  // last q with nnzoff[q] <= e
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (nnzoff[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int64_t nu = segu[lo + 1] - segu[lo], nm = segm[lo + 1] - segm[lo];
+        const int32_t r = rows[e], c = cols[e];
+        if (r < 0 || r >= nu || c < 0 || c >= nm) {
+            atomicAdd(flag, 1);
+            rows[e] = -1;
+            cols[e] = -1;
+        } else {
+            rows[e] = (int32_t)(r + segu[lo]);
+            cols[e] = (int32_t)(c + segm[lo]);
+        }
+    }
+}
+
+__global__ void k_rowprob(const int64_t *__restrict__ segu, const int64_t *__restrict__ segm, int n_prob, int64_t n_u,
+                          int64_t n, int32_t *__restrict__ rowprob) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t *seg = i < n_u ? segu : segm;
+        const int64_t v = i < n_u ? i : i - n_u;
+        int lo = 0, hi = n_prob;  // last q with seg[q] <= v
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (seg[mid] <= v) lo = mid; else hi = mid;
+        }
+        rowprob[i] = lo;
+    }
+}
+}  // namespace
+
+als_status launch_offset_ids(als_ctx *c, const int64_t *nnzoff, int n_prob, const int64_t *segu, const int64_t *segm,
+                             int32_t *rows, int32_t *cols, int64_t nnz, int *flag) {
+    if (nnz <= 0) return ALS_OK;
+    k_offset_ids<<<grid_for(c, nnz, 256), 256, 0, c->stream>>>(nnzoff, n_prob, segu, segm, rows, cols, nnz, flag);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+als_status launch_rowprob(als_ctx *c) {
+    const int64_t n = c->n_u + c->n_m;
+    k_rowprob<<<grid_for(c, n, 256), 256, 0, c->stream>>>(c->segu, c->segm, c->n_prob, c->n_u, n, c->rowprob);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }

@@ -180,7 +180,7 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
     const int G = 128 / TPR;
     const size_t smem = (size_t)G * group_smem_elems<T>(a.nf) * sizeof(T);
     auto kern = k_sweep_fma<T, TPR, MAXE, WARM>;
-    ALS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (raise_smem_limit((const void *)kern, smem) != ALS_OK) return ALS_ECUDA;
     ALS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     int occ = 0;
@@ -192,7 +192,7 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
     // one row group per CTA: the hardware packs as many CTAs per SM as fit
     const int64_t want = (a.nrows + G - 1) / G;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)INT32_MAX));
-    kern<<<grid, 128, smem, c->stream>>>(a);
+    kern<<<grid, 128, smem, a.stream ? a.stream : c->stream>>>(a);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
@@ -228,12 +228,15 @@ als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc) {
     return sweep_launch<float, 128, 65, true>(c, a);
 }
 
-als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64) {
+als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst,
+                          cudaStream_t stream) {
     if (rows <= 0) return ALS_OK;
     const int64_t n = rows * ALS_TC_LD;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 8));
-    if (f64) k_to_bf16<double><<<g, 256, 0, c->stream>>>((const double *)F, rows, c->ld, c->shadow);
-    else k_to_bf16<float><<<g, 256, 0, c->stream>>>((const float *)F, rows, c->ld, c->shadow);
+    __nv_bfloat16 *out = dst ? dst : c->shadow;
+    cudaStream_t st = stream ? stream : c->stream;
+    if (f64) k_to_bf16<double><<<g, 256, 0, st>>>((const double *)F, rows, c->ld, out);
+    else k_to_bf16<float><<<g, 256, 0, st>>>((const float *)F, rows, c->ld, out);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }

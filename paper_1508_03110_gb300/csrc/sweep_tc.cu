@@ -320,7 +320,7 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
     // columns = the SM's 512) resident per SM, so tcgen05.alloc never waits.
     size_t smem = (size_t)L.total + 1024;
     if (smem < 46 * 1024) smem = 46 * 1024;
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (raise_smem_limit((const void *)k_sweep_tc, smem) != ALS_OK) return ALS_ECUDA;
     // the whole L1/shared array as shared memory, so that 4 CTAs fit per SM
     ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
@@ -328,7 +328,7 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
     // many CTAs resident per SM as shared memory allows (at most 4 here), and
     // each one holds its TMEM columns only for the row it solves.
     const int64_t grid = std::min<int64_t>(a.nrows, (int64_t)INT32_MAX);
-    k_sweep_tc<<<(unsigned)grid, TC_THREADS, smem, c->stream>>>(a, ntc);
+    k_sweep_tc<<<(unsigned)grid, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }

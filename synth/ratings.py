@@ -223,6 +223,30 @@ def make_config(name, **over):
                         cfg["rank"], cfg["n_f"], cfg["lam"], cfg["seed"])
 
 
+def make_batch(n_prob, nnz_lo, nnz_hi, dens_lo, dens_hi, seed, rank=10):
+    """Independent problems of uneven size: ratings log-uniform in [nnz_lo,
+    nnz_hi], density uniform in [dens_lo, dens_hi], 2-8 users per item, Zipf
+    degrees (users 1.1, items 1.0), half-star values.  Returns a list of
+    (n_u, n_m, rows, cols, vals) with ids local to each problem."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    probs = []
+    for _ in range(n_prob):
+        nnz = int(np.exp(rng.uniform(np.log(nnz_lo), np.log(nnz_hi))))
+        dens = rng.uniform(dens_lo, dens_hi)
+        ratio = rng.uniform(2.0, 8.0)
+        cells = nnz / dens
+        n_m = max(4, int(np.sqrt(cells / ratio)))
+        n_u = max(4, int(cells / n_m))
+        nnz = max(n_u, min(nnz, n_u * n_m // 2))
+        deg = rank_degrees(n_u, nnz, 1, n_m, rng, 1.1)
+        w = np.arange(1, n_m + 1, dtype=np.float64) ** -1.0
+        w = w[rng.permutation(n_m)]
+        rows, cols = sample_distinct(deg, w, rng)
+        vals = half_star_values(rows, cols, n_u, n_m, rank, rng)
+        probs.append((n_u, n_m, rows, cols, vals))
+    return probs
+
+
 def init_factors(n_u, n_m, n_f, seed):
     """x_0 (Eq. 5 layout, n_u rows then n_m rows of n_f): i.i.d. N(0, 1/n_f)."""
     rng = np.random.Generator(np.random.PCG64(seed))
