@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--workload", default="ml20m")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--gram", default="auto", choices=["auto", "fma", "tc"])
-    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--refine", type=int, default=2, help="maximum refinement corrections per row")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")

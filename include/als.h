@@ -92,7 +92,10 @@ typedef struct {
     double ls_tau;            /* Algorithm 3 shrink factor (paper: 0.9)      */
     double ls_c;              /* Algorithm 3 sufficient decrease (paper: 0.5)*/
     int32_t ls_max_shrinks;   /* shrink limit before the ALS fallback (200)  */
-    int32_t refine_steps;     /* ALS_MIXED: residual corrections per solve   */
+    int32_t refine_steps;     /* ALS_MIXED: most residual corrections per row
+                                 solve (2, 1..8); after the first, another is
+                                 taken only while the last one exceeded 2^-8
+                                 of the row (fold-in, a cold start: one more) */
     int32_t gram_path;        /* als_gram_path                                */
     size_t hbm_budget_bytes;  /* 0 = no limit                                 */
     als_alloc_fn alloc;

@@ -52,7 +52,7 @@ class _Buf:
             self.on_device = 0
 
 
-def make_config(n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=1, gram_path="auto",
+def make_config(n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=2, gram_path="auto",
                 hbm_budget_bytes=0, ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
     """An als_config with the library defaults and the given fields."""
     cfg = _lib.Config()
@@ -77,7 +77,7 @@ class ALS:
     """
 
     def __init__(self, n_u, n_m, rows, cols, vals, n_f, lam, precision="fp64", ls_mode="backtrack",
-                 refine_steps=1, gram_path="auto", hbm_budget_bytes=0, stream=None, rowptr=None,
+                 refine_steps=2, gram_path="auto", hbm_budget_bytes=0, stream=None, rowptr=None,
                  ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
         torch = _torch()
         self.lib = _lib.load()
@@ -273,7 +273,7 @@ class ALSBatch(ALS):
     Vectors use the global layout: every problem's U rows, then every
     problem's M rows."""
 
-    def __init__(self, problems, n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=1,
+    def __init__(self, problems, n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=2,
                  gram_path="auto", hbm_budget_bytes=0, stream=None):
         torch = _torch()
         self.lib = _lib.load()

@@ -358,7 +358,7 @@ extern "C" void als_config_default(als_config *cfg) {
     cfg->ls_tau = 0.9;
     cfg->ls_c = 0.5;
     cfg->ls_max_shrinks = 200;
-    cfg->refine_steps = 1;
+    cfg->refine_steps = 2;
     cfg->gram_path = ALS_GRAM_AUTO;
 }
 

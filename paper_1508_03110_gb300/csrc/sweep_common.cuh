@@ -87,6 +87,44 @@ __device__ void sw_trisolve(const T *A, int ldA, int nf, const T *diag, T *b, T 
     sw_gsync<TPR>();
 }
 
+// Stopping test of the mixed form's refinement u <- u + Ahat^-1 (v - A u):
+// true when the last correction dx is at most 2^-8 of the row.  What a
+// correction leaves is at most rho |dx| with rho = |I - Ahat^-1 A| (about
+// 2e-4 for a BF16-split tensor-core Gram accumulated over 3e4 ratings, 1e-5
+// for light rows), so after a correction this small the row is within
+// ~1e-6 of the exact solve -- below the mixed form's FP32 storage floor.
+// One group of TPR threads (a warp, or the CTA when TPR > 32); red: 2 * TPR /
+// 32 elements of scratch for the CTA case.
+template <typename T, int TPR>
+__device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int nf, T *red, int t) {
+    T d2 = T(0), u2 = T(0);
+    for (int k = t; k < nf; k += TPR) {
+        d2 = fma(dx[k], dx[k], d2);
+        u2 = fma(u[k], u[k], u2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+    }
+    if constexpr (TPR > 32) {
+        if ((t & 31) == 0) {
+            red[2 * (t >> 5)] = d2;
+            red[2 * (t >> 5) + 1] = u2;
+        }
+        __syncthreads();
+        d2 = T(0);
+        u2 = T(0);
+#pragma unroll
+        for (int w = 0; w < TPR / 32; ++w) {
+            d2 += red[2 * w];
+            u2 += red[2 * w + 1];
+        }
+        __syncthreads();
+    }
+    return d2 <= T(0x1p-16) * u2;
+}
+
 // ---------------------------------------------------------------------------
 // Blocked right-looking Cholesky (panels of 16 columns) for n <= 128, FP32,
 // by a CTA of exactly 128 threads.  Panel: thread t holds row kb+t of the
@@ -178,218 +216,34 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
     return true;
 }
 
-// L L^T x = b with L from chol_blocked128 (diag = reciprocals), blocks of 16: the diagonal block
-// is solved by warp 0 with shuffles, the rows outside it are updated by all
-// 128 threads.  b is consumed; z is scratch; x receives the solution (x may
-// alias z).
-__device__ __forceinline__ void trisolve_blocked128(const float *A, int ldA, int n, const float *diag, float *b,
-                                                    float *z, float *x, int t) {
-    const int warp = t >> 5, lane = t & 31;
-    for (int kb = 0; kb < n; kb += 16) {
-        const int nb = min(16, n - kb);
-        __syncthreads();
-        if (warp == 0) {
-            float bv = lane < nb ? b[kb + lane] : 0.0f;
-            for (int c = 0; c < nb; ++c) {
-                const float zc = __shfl_sync(0xffffffffu, bv, c) * diag[kb + c];
-                if (lane == c) z[kb + c] = zc;
-                if (lane > c && lane < nb) bv -= A[(kb + lane) * ldA + kb + c] * zc;
-            }
-        }
-        __syncthreads();
-        for (int i = kb + nb + t; i < n; i += 128) {
-            float s = 0.0f;
-            for (int c = 0; c < nb; ++c) s = fmaf(A[i * ldA + kb + c], z[kb + c], s);
-            b[i] -= s;
-        }
-    }
-    const int last = ((n - 1) / 16) * 16;
-    for (int kb = last; kb >= 0; kb -= 16) {
-        const int nb = min(16, n - kb);
-        __syncthreads();
-        if (warp == 0) {
-            float zv = lane < nb ? z[kb + lane] : 0.0f;
-            for (int c = nb - 1; c >= 0; --c) {
-                const float xc = __shfl_sync(0xffffffffu, zv, c) * diag[kb + c];
-                if (lane == c) x[kb + c] = xc;
-                if (lane < c) zv -= A[(kb + c) * ldA + kb + lane] * xc;
-            }
-        }
-        __syncthreads();
-        for (int i = t; i < kb; i += 128) {
-            float s = 0.0f;
-            for (int c = 0; c < nb; ++c) s = fmaf(A[(kb + c) * ldA + i], x[kb + c], s);
-            z[i] -= s;
-        }
-    }
-    __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// Blocked Cholesky with inverted diagonal blocks, n <= 128, FP32, exactly 128
-// threads.  Per panel of 16 columns:
-//   1. warp 0 factors the 16 x 16 diagonal block warp-synchronously (lane i
-//      holds row i; pivots and column entries move by shuffles), then each
-//      lane j computes column j of the block's inverse, which overwrites the
-//      block (lower triangle) -- the solves only need the inverse;
-//   2. every row below the block: L21 row = A21 row * inv(L_kk)^T (a 16-wide
-//      matvec per thread, no dependency chain), stored in A and transposed
-//      into PT;
-//   3. trailing update A22 -= L21 L21^T with 4 x 4 register blocks.
-// Three CTA barriers per panel.  On return: off-diagonal blocks of A hold L,
-// diagonal blocks hold inv(L_kk), diag[k] = 1 / L[k][k].  work: >= 16*128 + 4
-// floats, 16-byte aligned.  Returns false (in every thread) on a
-// non-positive pivot.
-__device__ __forceinline__ bool chol_inv128(float *A, int ldA, int n, float *diag, float *work, int t) {
-    float *PT = work;                                     // [16][128]
-    int *flag = reinterpret_cast<int *>(work + 16 * 128);  // non-SPD flag
-    const int warp = t >> 5, lane = t & 31;
-    if (t == 0) *flag = 0;
-    for (int kb = 0; kb < n; kb += 16) {
-        const int nb = min(16, n - kb), mp = n - kb;
-        __syncthreads();
-        if (warp == 0) {
-            float row[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) row[c] = (lane < nb && c < nb) ? A[(kb + lane) * ldA + kb + c] : 0.0f;
-            bool bad = false;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                if (c < nb) {
-                    const float p = __shfl_sync(0xffffffffu, row[c], c);
-                    if (!(p > 0.0f)) bad = true;
-                    const float rd = rsqrtf(p);
-                    const float l = (lane > c) ? row[c] * rd : 0.0f;
-                    if (lane > c) row[c] = l;
-                    if (lane == c) {
-                        row[c] = p * rd;
-                        diag[kb + c] = rd;
-                    }
-#pragma unroll
-                    for (int cc = c + 1; cc < 16; ++cc) {
-                        const float lcc = __shfl_sync(0xffffffffu, l, cc);
-                        if (lane >= cc) row[cc] -= l * lcc;
-                    }
-                }
-            }
-            if (bad && lane == 0) *flag = 1;
-            // L_kk into shared memory, then column `lane` of its inverse
-            if (lane < nb) {
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c <= lane) A[(kb + lane) * ldA + kb + c] = row[c];
-            }
-            __syncwarp();
-            float inv[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float v = 0.0f;
-                if (i < nb && i >= lane) {
-                    if (i == lane) {
-                        v = diag[kb + i];
-                    } else {
-                        float s = 0.0f;
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            if (c >= lane && c < i) s = fmaf(A[(kb + i) * ldA + kb + c], inv[c], s);
-                        v = -s * diag[kb + i];
-                    }
-                }
-                inv[i] = v;
-            }
-            __syncwarp();
-            if (lane < nb) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (i < nb && i >= lane) A[(kb + i) * ldA + kb + lane] = inv[i];
-            }
-        }
-        __syncthreads();
-        if (*flag) return false;
-        // rows below the diagonal block: L21 = A21 inv(L_kk)^T
-        {
-            float l[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) l[c] = 0.0f;
-            if (t >= nb && t < mp) {
-                float a21[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) a21[c] = (c < nb) ? A[(kb + t) * ldA + kb + c] : 0.0f;
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    if (c < nb) {
-                        float s = 0.0f;
-#pragma unroll
-                        for (int cc = 0; cc <= c; ++cc) s = fmaf(a21[cc], A[(kb + c) * ldA + kb + cc], s);
-                        l[c] = s;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < nb) A[(kb + t) * ldA + kb + c] = l[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) PT[c * 128 + t] = l[c];
-        }
-        __syncthreads();
-        const int m = mp - nb;
-        if (m > 0) {
-            const int mb = (m + 3) >> 2, nblk = mb * (mb + 1) / 2;
-            for (int bidx = t; bidx < nblk; bidx += 128) {
-                int bi = (int)((sqrtf(8.0f * (float)bidx + 1.0f) - 1.0f) * 0.5f);
-                while ((bi + 1) * (bi + 2) / 2 <= bidx) ++bi;
-                while (bi * (bi + 1) / 2 > bidx) --bi;
-                const int bj = bidx - bi * (bi + 1) / 2;
-                const int pi = nb + 4 * bi, pj = nb + 4 * bj;
-                float acc[4][4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const float4 li = *reinterpret_cast<const float4 *>(PT + c * 128 + pi);
-                    const float4 lj = *reinterpret_cast<const float4 *>(PT + c * 128 + pj);
-                    const float a4[4] = {li.x, li.y, li.z, li.w}, b4[4] = {lj.x, lj.y, lj.z, lj.w};
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a4[p], b4[q], acc[p][q]);
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int i = kb + pi + p;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = kb + pj + q;
-                        if (i < n && j <= i) A[i * ldA + j] -= acc[p][q];
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return true;
-}
-
-// L L^T x = b with A from chol_inv128 (inverted diagonal blocks): per block
-// a 16-wide triangular matvec with the inverse, then the update of the rows
-// outside the block, by all 128 threads.  b is consumed; z scratch; x result.
+// L L^T x = b with A from chol_blocked128 after invert_diag_blocks128 (the
+// diagonal blocks hold inv(L_kk)): per block of 16, z_blk = inv(L_kk) b_blk
+// by 16 threads, then the rows outside the block are updated by all 128
+// threads.  Every dot product is a fixed 16-term loop (predicated), so its
+// shared-memory loads issue together.  b is consumed; z scratch; x result.
 __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, float *b, float *z, float *x,
                                                 int t) {
     for (int kb = 0; kb < n; kb += 16) {
         const int nb = min(16, n - kb);
         __syncthreads();
         if (t < nb) {
-            float s = 0.0f;
-            for (int c = 0; c <= t; ++c) s = fmaf(A[(kb + t) * ldA + kb + c], b[kb + c], s);
-            z[kb + t] = s;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                if (c <= t) s0 = fmaf(A[(kb + t) * ldA + kb + c], b[kb + c], s0);
+                if (c + 1 <= t) s1 = fmaf(A[(kb + t) * ldA + kb + c + 1], b[kb + c + 1], s1);
+            }
+            z[kb + t] = s0 + s1;
         }
         __syncthreads();
         for (int i = kb + nb + t; i < n; i += 128) {
-            float s = 0.0f;
-            for (int c = 0; c < nb; ++c) s = fmaf(A[i * ldA + kb + c], z[kb + c], s);
-            b[i] -= s;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                if (c < nb) s0 = fmaf(A[i * ldA + kb + c], z[kb + c], s0);
+                if (c + 1 < nb) s1 = fmaf(A[i * ldA + kb + c + 1], z[kb + c + 1], s1);
+            }
+            b[i] -= s0 + s1;
         }
     }
     const int last = ((n - 1) / 16) * 16;
@@ -397,15 +251,23 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
         const int nb = min(16, n - kb);
         __syncthreads();
         if (t < nb) {
-            float s = 0.0f;
-            for (int c = t; c < nb; ++c) s = fmaf(A[(kb + c) * ldA + kb + t], z[kb + c], s);
-            x[kb + t] = s;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                if (c >= t && c < nb) s0 = fmaf(A[(kb + c) * ldA + kb + t], z[kb + c], s0);
+                if (c + 1 >= t && c + 1 < nb) s1 = fmaf(A[(kb + c + 1) * ldA + kb + t], z[kb + c + 1], s1);
+            }
+            x[kb + t] = s0 + s1;
         }
         __syncthreads();
         for (int i = t; i < kb; i += 128) {
-            float s = 0.0f;
-            for (int c = 0; c < nb; ++c) s = fmaf(A[(kb + c) * ldA + i], x[kb + c], s);
-            z[i] -= s;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                if (c < nb) s0 = fmaf(A[(kb + c) * ldA + i], x[kb + c], s0);
+                if (c + 1 < nb) s1 = fmaf(A[(kb + c + 1) * ldA + i], x[kb + c + 1], s1);
+            }
+            z[i] -= s0 + s1;
         }
     }
     __syncthreads();

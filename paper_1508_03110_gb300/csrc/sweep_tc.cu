@@ -53,7 +53,7 @@ __host__ __device__ inline TcLayout tc_layout(int nf) {
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
     L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
-    L.mbar = L.vec + (5 * 128 + 2320) * 4;
+    L.mbar = L.vec + (5 * 128 + 16 * 128 + 256 + 16) * 4;
     L.holder = L.mbar + 16;
     L.total = L.holder + 16;
     return L;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
             for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             for (int s = 1; s < a.refine; ++s) {
-                __syncthreads();
+                if (sw_correction_small<float, TC_THREADS>(colk, u, nf, part, t)) break;
                 float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) uk[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;

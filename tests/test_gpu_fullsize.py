@@ -1,0 +1,141 @@
+"""Parity at the full benchmark size (138,493 users x 26,744 items, 2e7
+ratings, n_f = 100) in the benchmark's launch configuration (mixed precision,
+tensor-core Gram, one refinement step), and of the FP64 form at the same size.
+The oracle cannot run whole ALS-NCG iterations here in seconds, so it checks
+what it can compute at this size: every rating's contribution to the gradient
+and to Q(alpha) (one pass each), and exact per-row solves of Eq. (3)/(4) for
+sampled rows (the heaviest, the lightest and every 997-th row in degree
+order), given the same input factors as the GPU.
+
+Tolerances:
+  * FP64 form: 1e-10 relative (per sampled row, per vector, per coefficient);
+  * mixed form, one-pass quantities (gradient, Q coefficients) from the same
+    FP32-representable inputs: 1e-5 relative -- FP32 products and
+    compensated FP32 sums over up to 33k ratings, FP64 totals;
+  * mixed sweep rows: the refinement from the current row u0 leaves an error
+    of at most rho * |u* - u0| with rho = |I - A_bf16^-1 A|, of order
+    kappa(A_i) * 2^-16; from a random start (|u* - u0| ~ |u*|) the bound
+    used is 5e-2 |u* - u0| per row (the same as the small-case test);
+  * mixed vs FP64 GPU run: f within 1e-5 relative at equal iteration count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    r = synth.make_config("ml20m")
+    P = oracle.build_problem(r.n_u, r.n_m, r.n_f, r.lam, r.rows, r.cols, r.vals)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    return r, P, x0
+
+
+def _model(r, **kw):
+    from paper_1508_03110_gb300 import ALS
+    return ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, **kw)
+
+
+def _sample(order):
+    order = np.asarray(order)
+    return np.unique(np.concatenate([order[:4], order[::997], order[-4:]]))
+
+
+def _row_rel(a, b, scale=None):
+    """max over rows of |a - b| / |scale| (scale defaults to b)."""
+    s = b if scale is None else scale
+    num = np.linalg.norm(a - b, axis=1)
+    den = np.maximum(np.linalg.norm(s, axis=1), 1e-300)
+    return float(np.max(num / den))
+
+
+def test_fullsize_builder_bit_exact(big):
+    r, P, _ = big
+    with _model(r, precision="mixed") as m:
+        R = m.ratings()
+    for k in ("uptr", "uidx", "mptr", "midx"):
+        assert np.array_equal(R[k], getattr(P, k)), k
+    assert np.array_equal(R["uval"].astype(np.float64), P.uval)
+    assert np.array_equal(R["mval"].astype(np.float64), P.mval)
+
+
+def test_fullsize_fp64_sweep_sampled_rows(big):
+    r, P, x0 = big
+    nf = r.n_f
+    with _model(r, precision="fp64") as m:
+        R = m.ratings()
+        m.set_x(x0)
+        m.sweep(1)
+        x1 = m.get_x()
+    U1 = x1[: r.n_u * nf].reshape(r.n_u, nf)
+    M1 = x1[r.n_u * nf:].reshape(r.n_m, nf)
+    su, sm = _sample(R["uorder"]), _sample(R["morder"])
+    ref_u = oracle.solve_rows(P, 0, x0[r.n_u * nf:], su).reshape(-1, nf)
+    assert _row_rel(U1[su], ref_u) < 1e-10
+    ref_m = oracle.solve_rows(P, 1, U1.reshape(-1), sm).reshape(-1, nf)   # M half from the GPU's U
+    assert _row_rel(M1[sm], ref_m) < 1e-10
+
+
+def test_fullsize_fp64_grad_and_q(big):
+    r, P, x0 = big
+    p = synth.init_factors(r.n_u, r.n_m, r.n_f, 12)
+    with _model(r, precision="fp64") as m:
+        m.set_x(x0)
+        g, gn = m.grad()
+        c = m.linesearch_coeffs(p)
+    gref = oracle.grad(P, x0)
+    assert np.linalg.norm(g - gref) <= 1e-10 * np.linalg.norm(gref)
+    cref = oracle.ls_coeffs(P, x0, p)
+    assert np.all(np.abs(c - cref) <= 1e-10 * np.maximum(np.abs(cref), 1e-12 * np.abs(cref).max()))
+
+
+def test_fullsize_mixed_one_pass_quantities(big):
+    r, P, x0 = big
+    xf = x0.astype(np.float32).astype(np.float64)          # the mixed form stores FP32 factors
+    p = synth.init_factors(r.n_u, r.n_m, r.n_f, 12).astype(np.float32).astype(np.float64)
+    with _model(r, precision="mixed") as m:
+        m.set_x(xf)
+        g, _ = m.grad()
+        c = m.linesearch_coeffs(p)
+        f = m.loss()
+    gref = oracle.grad(P, xf)
+    assert np.linalg.norm(g - gref) <= 1e-5 * np.linalg.norm(gref)
+    cref = oracle.ls_coeffs(P, xf, p)
+    assert np.all(np.abs(c - cref) <= 1e-5 * np.abs(cref).max())
+    assert abs(f - oracle.loss(P, xf)) <= 1e-6 * abs(f)
+
+
+def test_fullsize_mixed_sweep_sampled_rows(big):
+    r, P, x0 = big
+    nf = r.n_f
+    xf = x0.astype(np.float32).astype(np.float64)
+    with _model(r, precision="mixed") as m:
+        R = m.ratings()
+        m.set_x(xf)
+        m.sweep(1)
+        x1 = m.get_x()
+    U0 = xf[: r.n_u * nf].reshape(r.n_u, nf)
+    U1 = x1[: r.n_u * nf].reshape(r.n_u, nf)
+    M0 = xf[r.n_u * nf:].reshape(r.n_m, nf)
+    M1 = x1[r.n_u * nf:].reshape(r.n_m, nf)
+    su, sm = _sample(R["uorder"]), _sample(R["morder"])
+    ref_u = oracle.solve_rows(P, 0, M0.reshape(-1), su).reshape(-1, nf)
+    assert _row_rel(U1[su], ref_u, scale=ref_u - U0[su]) < 5e-2
+    U1f = U1.astype(np.float32).astype(np.float64)
+    ref_m = oracle.solve_rows(P, 1, U1f.reshape(-1), sm).reshape(-1, nf)
+    assert _row_rel(M1[sm], ref_m, scale=ref_m - M0[sm]) < 5e-2
+
+
+def test_fullsize_mixed_f_matches_fp64_run(big):
+    r, _, x0 = big
+    fs = {}
+    for prec in ("fp64", "mixed"):
+        with _model(r, precision=prec) as m:
+            m.set_x(x0)
+            fs[prec] = [m.step()["f"] for _ in range(3)]
+    f64, fmx = np.array(fs["fp64"]), np.array(fs["mixed"])
+    assert np.all(np.abs(fmx - f64) <= 1e-5 * np.abs(f64)), np.abs(fmx - f64) / np.abs(f64)
