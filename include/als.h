@@ -94,8 +94,10 @@ typedef struct {
     int32_t ls_max_shrinks;   /* shrink limit before the ALS fallback (200)  */
     int32_t refine_steps;     /* ALS_MIXED: most residual corrections per row
                                  solve (2, 1..8); after the first, another is
-                                 taken only while the last one exceeded 2^-8
-                                 of the row (fold-in, a cold start: one more) */
+                                 taken only while what the last one may have
+                                 left, (2^-17 + n 2^-24) times its size for a
+                                 row of n ratings, exceeds 2^-21 of the row
+                                 (fold-in, a cold start: one more) */
     int32_t gram_path;        /* als_gram_path                                */
     size_t hbm_budget_bytes;  /* 0 = no limit                                 */
     als_alloc_fn alloc;

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
             } else {
                 for (int k = t; k < nf; k += TPR) u[k] = xi ? xi[k] : T(0);
                 for (int s = 0; s < a.refine; ++s) {
-                    if (s > 0 && sw_correction_small<T, TPR>(colk, u, nf, err, t)) break;
+                    if (s > 0 && sw_correction_small<T, TPR>(colk, u, nf, n, err, t)) break;
                     // res = sum_e f_e (r_e - f_e . u) - lambda n u
                     T rv = T(0), rcmp = T(0);
                     for (int c0 = 0; c0 < n; c0 += CH) {

@@ -87,16 +87,18 @@ __device__ void sw_trisolve(const T *A, int ldA, int nf, const T *diag, T *b, T 
     sw_gsync<TPR>();
 }
 
-// Stopping test of the mixed form's refinement u <- u + Ahat^-1 (v - A u):
-// true when the last correction dx is at most 2^-8 of the row.  What a
-// correction leaves is at most rho |dx| with rho = |I - Ahat^-1 A| (about
-// 2e-4 for a BF16-split tensor-core Gram accumulated over 3e4 ratings, 1e-5
-// for light rows), so after a correction this small the row is within
-// ~1e-6 of the exact solve -- below the mixed form's FP32 storage floor.
+// Stopping test of the mixed form's refinement u <- u + Ahat^-1 (v - A u)
+// for a row with n ratings: true when rho(n) |dx| <= 2^-21 |u|, dx the last
+// correction.  A correction leaves at most rho |dx|, rho = |I - Ahat^-1 A|;
+// rho(n) = 2^-17 + n 2^-24 bounds it from above -- the BF16 split's own error
+// plus FP32 accumulation over n ratings (measured at ML20M size: 2e-6 for
+// rows of ~150 ratings, 8e-6 at 9e3, 1.7e-4 at 3.2e4, each under the bound).
+// So a row stops once what is left is below ~5e-7 of it, under the mixed
+// form's FP32 storage floor; light rows rarely need a second correction.
 // One group of TPR threads (a warp, or the CTA when TPR > 32); red: 2 * TPR /
 // 32 elements of scratch for the CTA case.
 template <typename T, int TPR>
-__device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int nf, T *red, int t) {
+__device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int nf, int n, T *red, int t) {
     T d2 = T(0), u2 = T(0);
     for (int k = t; k < nf; k += TPR) {
         d2 = fma(dx[k], dx[k], d2);
@@ -122,15 +124,17 @@ __device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int
         }
         __syncthreads();
     }
-    return d2 <= T(0x1p-16) * u2;
+    const T rho = T(0x1p-17) + T(n) * T(0x1p-24);
+    return d2 * rho * rho <= T(0x1p-42) * u2;
 }
 
 // ---------------------------------------------------------------------------
 // Blocked right-looking Cholesky (panels of 16 columns) for n <= 128, FP32,
 // by a CTA of exactly 128 threads.  Panel: thread t holds row kb+t of the
 // panel in registers, one column at a time (pivot, scale, rank-1 update of
-// the panel).  Trailing update A22 -= L21 L21^T with 4x4 register blocks
-// from the transposed panel PT in shared memory.
+// the panel).  Trailing update A22 -= L21 L21^T by row strips of 16 columns
+// from the transposed panel PT in shared memory (a strip's columns end at
+// 16 ceil((n - kb - 16) / 16) + 15 <= 127 for n <= 128: inside PT's rows).
 // A: lower triangle used; on return its lower triangle holds L (diagonal
 // included) and diag[k] = 1 / L[k][k] (reciprocal, for the solves).  work: >= 16*128 + 256 + 2 floats, 16-byte
 // aligned.  Returns false (in every thread) on a non-positive pivot.
@@ -178,37 +182,40 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
         __syncthreads();
         const int m = mp - nb;
         if (m > 0) {
-            const int mb = (m + 3) >> 2, nblk = mb * (mb + 1) / 2;
-            for (int bidx = t; bidx < nblk; bidx += 128) {
-                int bi = (int)((sqrtf(8.0f * (float)bidx + 1.0f) - 1.0f) * 0.5f);
-                while ((bi + 1) * (bi + 2) / 2 <= bidx) ++bi;
-                while (bi * (bi + 1) / 2 > bidx) --bi;
-                const int bj = bidx - bi * (bi + 1) / 2;
-                const int pi = nb + 4 * bi, pj = nb + 4 * bj;
-                float acc[4][4];
+            // trailing update by row strips: item (g, i) is row i of the
+            // trailing block, columns j0 = nb + 16 g .. j0 + 15 (j <= i kept);
+            // a warp takes consecutive rows of one strip, so the update of A
+            // (row stride ldA odd) is conflict-free and the strip's L21
+            // columns are broadcast loads
+            const int G = (m + 15) >> 4;
+            const int total = G * m - 8 * G * (G - 1);   // sum over g of (m - 16 g)
+            for (int q = t; q < total; q += 128) {
+                int g = 0, qq = q;
+                while (qq >= m - 16 * g) {
+                    qq -= m - 16 * g;
+                    ++g;
+                }
+                const int i = nb + 16 * g + qq, j0 = nb + 16 * g;
+                float acc[16];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+                for (int k = 0; k < 16; ++k) acc[k] = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    const float4 li = *reinterpret_cast<const float4 *>(PT + c * 128 + pi);
-                    const float4 lj = *reinterpret_cast<const float4 *>(PT + c * 128 + pj);
-                    const float a4[4] = {li.x, li.y, li.z, li.w}, b4[4] = {lj.x, lj.y, lj.z, lj.w};
+                    const float li = PT[c * 128 + i];
+                    const float4 *lj = reinterpret_cast<const float4 *>(PT + c * 128 + j0);
 #pragma unroll
-                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a4[p], b4[q], acc[p][q]);
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int i = kb + pi + p;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = kb + pj + q;
-                        if (i < n && j <= i) A[i * ldA + j] -= acc[p][q];
+                    for (int v = 0; v < 4; ++v) {
+                        const float4 w = lj[v];
+                        acc[4 * v] = fmaf(li, w.x, acc[4 * v]);
+                        acc[4 * v + 1] = fmaf(li, w.y, acc[4 * v + 1]);
+                        acc[4 * v + 2] = fmaf(li, w.z, acc[4 * v + 2]);
+                        acc[4 * v + 3] = fmaf(li, w.w, acc[4 * v + 3]);
                     }
                 }
+                float *ar = A + (kb + i) * ldA + kb + j0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (j0 + k <= i) ar[k] -= acc[k];
             }
         }
         __syncthreads();

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
             for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             for (int s = 1; s < a.refine; ++s) {
-                if (sw_correction_small<float, TC_THREADS>(colk, u, nf, part, t)) break;
+                if (sw_correction_small<float, TC_THREADS>(colk, u, nf, n, part, t)) break;
                 float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) uk[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
