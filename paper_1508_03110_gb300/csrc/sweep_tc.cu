@@ -41,14 +41,15 @@ constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int TMEM_COLS = 128;
 
 struct TcLayout {
-    int ring, A, vec, mbar, holder, total;
+    int ring, meta, A, vec, mbar, holder, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int nf) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
-    int big = NSTAGE * STAGE_BYTES;
+    L.meta = NSTAGE * STAGE_BYTES;  // per stage: the chunk's ids, then its ratings
+    int big = L.meta + NSTAGE * KCH * 8;
     const int a_bytes = nf * (nf + 1) * 4;
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
@@ -64,57 +65,40 @@ __device__ __forceinline__ void ld4f(const float *p, float (&v)[4]) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-__device__ __forceinline__ float wsum(float x) {
+// acc += sum over q < 8 with 4 q < cnt of f_q (r_q - f_q . u), f_q the FP32
+// factor row of id ix[4 q] and r_q = vx[4 q]: the warp's share of the FP32
+// residual of the row's normal equations (lane = 4-wide slot of the row).
+// All eight rows are requested before any is used, so one gather latency
+// covers them.
+__device__ __forceinline__ void resid8(const float *F, int ld, const int32_t *ix, const float *vx, int64_t cnt,
+                                       const float (&uu)[4], int lane, bool act, float (&acc)[4],
+                                       float (&cmp)[4]) {
+    float f[8][4], d[8], r[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// acc += sum over e in {e0, e0+4, e0+8, ...} < e1 of f_e (r_e - f_e . u): the
-// FP32 residual of the row's normal equations, one warp, lane = 4-wide slot;
-// four gathered rows in flight at a time.
-__device__ __forceinline__ void resid_range(const SweepArgs &a, const float *F, const float (&uu)[4], int64_t e,
-                                            int64_t e1, int lane, bool act, float (&acc)[4],
-                                            float (&cmp)[4]) {
-    for (; e + 12 < e1; e += 16) {
-        float f[4][4];
-        int64_t j[4];
+    for (int q = 0; q < 8; ++q) {
+        const bool in = 4 * q < cnt;
+        const int64_t j = in ? ix[4 * q] : 0;
+        r[q] = in ? vx[4 * q] : 0.0f;
+        if (in && act) ld4f(F + j * ld + 4 * lane, f[q]);
+        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
+    }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) j[q] = a.idx[e + 4 * q];
+    for (int q = 0; q < 8; ++q) {
+        d[q] = uu[0] * f[q][0];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (act) ld4f(F + j[q] * a.ld + 4 * lane, f[q]);
-            else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.f;
-        }
-        float d[4];
+        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
+    }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            d[q] = uu[0] * f[q][0];
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
-        }
+        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float er = a.val[e + 4 * q] - d[q];
+    for (int q = 0; q < 8; ++q) {
+        if (4 * q < cnt) {
+            const float er = r[q] - d[q];
 #pragma unroll
             for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
         }
-    }
-    for (; e < e1; e += 4) {
-        const int64_t j0 = a.idx[e];
-        float f0[4] = {0.f, 0.f, 0.f, 0.f};
-        if (act) ld4f(F + j0 * a.ld + 4 * lane, f0);
-        float d0 = uu[0] * f0[0];
-#pragma unroll
-        for (int i = 1; i < 4; ++i) d0 = fmaf(uu[i], f0[i], d0);
-        d0 = wsum(d0);
-        const float e0 = a.val[e] - d0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], e0 * f0[i]);
     }
 }
 
@@ -132,6 +116,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
     float *colk = vec, *v1 = vec + 128, *v2 = vec + 256, *u = vec + 384, *diag = vec + 512;
     float *part = vec + 640;   // residual partials (residual phase)
     float *work = vec + 640;   // Cholesky panel scratch (factorisation phase)
+    int32_t *meta_i = reinterpret_cast<int32_t *>(base + L.meta);          // [NSTAGE][KCH]
+    float *meta_v = reinterpret_cast<float *>(base + L.meta + NSTAGE * KCH * 4);
     const uint32_t mbar[2] = {sbase + L.mbar, sbase + L.mbar + 8};
     uint32_t *holder = reinterpret_cast<uint32_t *>(base + L.holder);
 
@@ -172,25 +158,45 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             //      while the chunk's copies and MMAs are in flight -------------
             const int nch = (n + KCH - 1) / KCH;
             int pend[2] = {0, 0};
-            auto gather = [&](int ch, int st) {
+            // ids and ratings of the next chunk to gather: thread t copies
+            // ratings k0 + 8 j (j < 4) of a chunk, k0 = (t / 16) % 8
+            const int k0 = (t >> 4) & 7;
+            int32_t pj[4];
+            float pv[4];
+            auto prefetch = [&](int ch) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t e = beg + (int64_t)ch * KCH + k0 + 8 * j;
+                    const bool in = ch < nch && e < beg + n;
+                    pj[j] = in ? a.idx[e] : -1;
+                    pv[j] = in ? a.val[e] : 0.0f;
+                }
+            };
+            auto gather = [&](int st) {
                 const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
-                const int64_t e0 = beg + (int64_t)ch * KCH, e_end = beg + n;
 #pragma unroll
                 for (int i = 0; i < (2 * KCH * 16) / TC_THREADS; ++i) {
                     const int p = t + TC_THREADS * i;
                     const int part_ = p >> 9, k = (p >> 4) & (KCH - 1), q = p & 15;
                     const uint32_t dst = stage + part_ * TILE_BYTES + (k >> 3) * SBO + (q >> 3) * LBO + (k & 7) * 128 +
                                          ((uint32_t)((q & 7) ^ (k & 7)) << 4);
-                    if (e0 + k < e_end) {
-                        const int64_t j = a.idx[e0 + k];
-                        cp_async16(dst, Fb + j * (2 * ALS_TC_LD) + part_ * ALS_TC_LD + q * 8);
-                    } else {
-                        cp_async16_zero(dst, Fb);
-                    }
+                    const int32_t j = pj[i & 3];
+                    if (j >= 0) cp_async16(dst, Fb + (int64_t)j * (2 * ALS_TC_LD) + part_ * ALS_TC_LD + q * 8);
+                    else cp_async16_zero(dst, Fb);
                 }
                 cp_async_commit();
+                if ((t & 15) == 0) {  // the chunk's ids and ratings for its residual
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        meta_i[st * KCH + k0 + 8 * j] = pj[j];
+                        meta_v[st * KCH + k0 + 8 * j] = pv[j];
+                    }
+                }
             };
-            gather(0, 0);
+            prefetch(0);
+            gather(0);
+            prefetch(1);
+            __syncthreads();  // chunk 0's ids and ratings visible to every warp
             for (int ch = 0; ch < nch; ++ch) {
                 const int st = ch & 1;
                 if (ch + 1 < nch) {
@@ -201,12 +207,13 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                         phase[sn] ^= 1u;
                         pend[sn] = 0;
                     }
-                    gather(ch + 1, sn);
+                    gather(sn);
+                    prefetch(ch + 2);
                 }
                 {
-                    const int64_t c0 = beg + (int64_t)ch * KCH;
-                    const int64_t c1 = (beg + n < c0 + KCH) ? beg + n : c0 + KCH;
-                    resid_range(a, F, uu, c0 + warp, c1, lane, act, acc, cmp);
+                    const int cnt = (n - ch * KCH < KCH) ? n - ch * KCH : KCH;
+                    resid8(F, a.ld, meta_i + st * KCH + warp, meta_v + st * KCH + warp, cnt - warp, uu, lane, act,
+                           acc, cmp);
                 }
                 if (ch + 1 < nch) cp_async_wait<1>();
                 else cp_async_wait<0>();
@@ -277,7 +284,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                 float uk[4], ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) uk[i] = (4 * lane + i < nf) ? u[4 * lane + i] : 0.0f;
-                resid_range(a, F, uk, beg + warp, beg + n, lane, act, ak, ck);
+                for (int64_t e = beg + warp; e < beg + n; e += 32)
+                    resid8(F, a.ld, a.idx + e, a.val + e, beg + n - e, uk, lane, act, ak, ck);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = ak[i] - ck[i];
                 __syncthreads();
