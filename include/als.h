@@ -321,6 +321,53 @@ ALS_API als_status als_server_stats(als_server *srv, double *p50_s, double *p99_
 /* Stop the worker after the queued work finishes and release everything. */
 ALS_API void als_server_destroy(als_server *srv);
 
+/* ---------------------------------------------------------------------------
+ * Launch shapes and the autotuner (the paper has neither; they fix how rows
+ * map onto this GPU).  Every shape computes the same quantities: the FP64
+ * form's results differ between shapes only in summation order, the mixed
+ * form's within its stated tolerances.
+ *   heavy_min      rows with at least this many ratings get a whole CTA in
+ *                  the gradient and Q-coefficient passes (others a lane group)
+ *   grid_mult      those passes' grids hold at most grid_mult x SM-count CTAs
+ *   sweep_bin_min  FMA sweep (n_f <= 32): rows with at least this many ratings
+ *                  are solved by a CTA, the others by a warp (0 = none)
+ *   split_min      rows with at least this many ratings are split into
+ *                  segments of about seg_len ratings whose partial Gram
+ *                  matrices and right-hand sides / residuals are formed by
+ *                  separate CTAs and added in FP64 (0 = no splitting)
+ *   gram_path      ALS_GRAM_FMA or ALS_GRAM_TC (the latter ALS_MIXED only)
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t heavy_min;        /* default 512    */
+    int32_t grid_mult;        /* default 32     */
+    int32_t sweep_bin_min;    /* default 0      */
+    int32_t split_min;        /* default 4096   */
+    int32_t seg_len;          /* default 2048, >= 32 */
+    int32_t gram_path;        /* in use         */
+} als_launch;
+
+ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);
+/* Apply launch shapes; ALS_EINVAL if out of range.  Captured iterations are
+ * recaptured on the next alsncg_step. */
+ALS_API als_status als_set_launch(als_ctx *ctx, const als_launch *in);
+
+typedef struct {
+    als_launch chosen;        /* the shapes kept                            */
+    int32_t candidates;       /* configurations timed                       */
+    double pass_ms_default;   /* gradient + Q passes, before / after (ms)   */
+    double pass_ms_tuned;
+    double sweep_ms_default;  /* one sweep P(x), before / after (ms)        */
+    double sweep_ms_tuned;
+} als_tune_report;
+
+/* Time candidate shapes on this context's own data, at its current factors
+ * and direction, one parameter group at a time (pass threshold and grid cap;
+ * Gram path where both apply; split threshold and segment length; FMA degree
+ * bin), and keep the fastest.  No factor, direction or NCG state is modified.
+ * reps (1..100): timed repetitions per candidate, best kept.  out may be
+ * NULL. */
+ALS_API als_status als_autotune(als_ctx *ctx, int32_t reps, als_tune_report *out);
+
 /* Wait for all work enqueued by this context. */
 ALS_API als_status als_sync(als_ctx *ctx);
 

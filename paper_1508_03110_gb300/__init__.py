@@ -263,6 +263,30 @@ class ALS:
                                        out.ctypes.data, dt, 0), "als_foldin")
         return out
 
+    def autotune(self, reps=3):
+        """Time candidate launch shapes on this problem and keep the fastest
+        (als_autotune); returns the shapes kept and the before/after times."""
+        r = _lib.TuneReport()
+        _lib.check(self.lib.als_autotune(self.ctx, int(reps), ctypes.byref(r)), "als_autotune")
+        out = {k: getattr(r, k) for k, _ in r._fields_ if k != "chosen"}
+        out.update({k: getattr(r.chosen, k) for k, _ in r.chosen._fields_})
+        return out
+
+    def get_launch(self):
+        l = _lib.Launch()
+        _lib.check(self.lib.als_get_launch(self.ctx, ctypes.byref(l)), "als_get_launch")
+        return {k: getattr(l, k) for k, _ in l._fields_}
+
+    def set_launch(self, **shape):
+        """Set launch shapes (als_set_launch); unspecified fields keep their value."""
+        l = _lib.Launch()
+        _lib.check(self.lib.als_get_launch(self.ctx, ctypes.byref(l)), "als_get_launch")
+        for k, v in shape.items():
+            if k == "gram_path" and isinstance(v, str):
+                v = {"fma": ALS_GRAM_FMA, "tc": ALS_GRAM_TC}[v]
+            setattr(l, k, int(v))
+        _lib.check(self.lib.als_set_launch(self.ctx, ctypes.byref(l)), "als_set_launch")
+
     def sync(self):
         _lib.check(self.lib.als_sync(self.ctx), "als_sync")
 

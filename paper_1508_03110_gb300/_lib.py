@@ -43,6 +43,21 @@ class IterInfo(ctypes.Structure):
     ]
 
 
+class Launch(ctypes.Structure):
+    _fields_ = [
+        ("heavy_min", ctypes.c_int32), ("grid_mult", ctypes.c_int32), ("sweep_bin_min", ctypes.c_int32),
+        ("split_min", ctypes.c_int32), ("seg_len", ctypes.c_int32), ("gram_path", ctypes.c_int32),
+    ]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [
+        ("chosen", Launch), ("candidates", ctypes.c_int32),
+        ("pass_ms_default", ctypes.c_double), ("pass_ms_tuned", ctypes.c_double),
+        ("sweep_ms_default", ctypes.c_double), ("sweep_ms_tuned", ctypes.c_double),
+    ]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [
         ("max_batch", ctypes.c_int32), ("max_batch_ratings", ctypes.c_int64), ("slots", ctypes.c_int32),
@@ -82,6 +97,9 @@ SIGNATURES = {
     "als_server_stats": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_i64),
                                 ctypes.POINTER(_dbl)]),
     "als_server_destroy": (None, [_vp]),
+    "als_get_launch": (_i32, [_vp, ctypes.POINTER(Launch)]),
+    "als_set_launch": (_i32, [_vp, ctypes.POINTER(Launch)]),
+    "als_autotune": (_i32, [_vp, _i32, ctypes.POINTER(TuneReport)]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
     "als_last_error": (ctypes.c_char_p, []),

@@ -12,6 +12,7 @@
 //   4. xbar = P(x_{k+1}) (U half, then M half), gbar_{k+1} = x_{k+1} - xbar;
 //   5. g_{k+1} = grad f(x_{k+1}) with gbar.g and gbar.(g_{k+1} - g_k) fused;
 //   6. beta-bar (Eq. 8), p_{k+1} = -gbar_{k+1} + beta-bar p_k.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -124,11 +125,30 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.refine = c->cfg.refine_steps;
     a.notspd = c->dflags;
     a.timeout = c->dflags + 7;
+    a.nbig = c->sweep_big[side];
     if (c->use_tc) {
         als_status s = launch_to_bf16(c, F, side ? c->n_u : c->n_m, c->f64);
         if (s != ALS_OK) return s;
     }
-    return launch_sweep(c, a, c->f64, c->use_tc);
+    const int64_t H = c->nsplit[side];
+    if (H == 0) return launch_sweep(c, a, c->f64, c->use_tc);
+    // the heaviest rows, split across CTAs, on the side stream; the rest, one
+    // CTA (or warp) each, beside them on the context's stream (inside a
+    // captured iteration the two become parallel branches of the graph)
+    ALS_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
+    ALS_CUDA_TRY(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    SweepArgs h = a;
+    h.stream = c->side_stream;
+    als_status s = launch_split_sweep(c, h, side);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaEventRecord(c->ev_join, c->side_stream));
+    a.order += H;
+    a.nrows -= H;
+    a.nbig = std::max<int64_t>(0, a.nbig - H);
+    s = launch_sweep(c, a, c->f64, c->use_tc);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    return ALS_OK;
 }
 
 // xbar = P(x) with gbar = x - xbar, or in place (x <- P(x)) when Xout == X.
@@ -466,6 +486,13 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        als_set_error("als_create: stream or event creation failed");
+        return fail(ALS_ECUDA);
+    }
     c->use_tc = !c->f64 && c->nf > 32 && cfg->gram_path != ALS_GRAM_FMA;
     if (cfg->gram_path == ALS_GRAM_TC && c->f64) { als_set_error("als_create: the tensor-core Gram needs ALS_MIXED"); return fail(ALS_EINVAL); }
     if (cfg->gram_path == ALS_GRAM_TC) c->use_tc = true;
@@ -570,6 +597,8 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
     } else {
         s = build_ratings(c, rows_or_null, rowptr_or_null, cols, vals, on_device);
     }
+    if (s != ALS_OK) return fail(s);
+    s = build_split(c);  // segment lists of the heaviest rows
     if (s != ALS_OK) return fail(s);
     if (cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return fail(ALS_ECUDA); }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -919,7 +948,207 @@ extern "C" void als_destroy(als_ctx *c) {
     while (!c->allocs.empty()) ctx_free(c, c->allocs.back().p);
     if (c->hS) cudaFreeHost(c->hS);
     if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: launch shapes timed on this context's own data.  Only launch
+// geometry changes (which kernel variant a row goes to, grid caps, the Gram
+// path of the mixed form); every variant computes the same quantities, so
+// the FP64 form's results change only in summation order.
+
+namespace {
+
+template <typename Fn>
+als_status time_best_ms(als_ctx *c, int reps, Fn &&fn, double *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ALS_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaGetLastError();
+        als_set_error("als_autotune: event creation failed");
+        return ALS_ECUDA;
+    }
+    als_status s = fn();  // warm-up
+    double best = 1e300;
+    for (int r = 0; r < reps && s == ALS_OK; ++r) {
+        cudaEventRecord(e0, c->stream);
+        s = fn();
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            als_set_error("als_autotune: timed launch failed");
+            s = ALS_ECUDA;
+            break;
+        }
+        float el = 0.0f;
+        cudaEventElapsedTime(&el, e0, e1);
+        best = std::min(best, (double)el);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return s;
+}
+
+// rows of `side` with at least t ratings (a prefix of the degree order)
+int64_t rows_at_least(const als_ctx *c, int side, int64_t t) {
+    const std::vector<int32_t> &d = c->h_deg[side];
+    return std::partition_point(d.begin(), d.end(), [&](int32_t x) { return (int64_t)x >= t; }) - d.begin();
+}
+
+}  // namespace
+
+namespace {
+
+void fill_launch(const als_ctx *c, als_launch *o) {
+    o->heavy_min = c->heavy_min;
+    o->grid_mult = c->grid_mult;
+    o->sweep_bin_min = c->sweep_bin_min;
+    o->split_min = c->split_min;
+    o->seg_len = c->seg_len;
+    o->gram_path = c->f64 ? ALS_GRAM_FMA : (c->use_tc ? ALS_GRAM_TC : ALS_GRAM_FMA);
+}
+
+// apply launch shapes (validated by the caller); rebuilds what depends on them
+als_status apply_launch(als_ctx *c, const als_launch &l) {
+    als_status s = load_degrees(c);
+    if (s != ALS_OK) return s;
+    c->heavy_min = l.heavy_min;
+    c->nheavy_u = rows_at_least(c, 0, l.heavy_min);
+    c->nheavy_m = rows_at_least(c, 1, l.heavy_min);
+    c->grid_mult = l.grid_mult;
+    c->sweep_bin_min = l.sweep_bin_min;
+    c->sweep_big[0] = l.sweep_bin_min > 0 ? rows_at_least(c, 0, l.sweep_bin_min) : 0;
+    c->sweep_big[1] = l.sweep_bin_min > 0 ? rows_at_least(c, 1, l.sweep_bin_min) : 0;
+    if (!c->f64) {
+        const bool tc = l.gram_path == ALS_GRAM_TC;
+        if (tc && !c->shadow) {
+            c->shadow_rows = std::max(c->n_u, c->n_m);
+            void *p = nullptr;
+            if ((s = ctx_alloc(c, &p, (size_t)c->shadow_rows * 2 * ALS_TC_LD * sizeof(__nv_bfloat16))) != ALS_OK)
+                return s;
+            c->shadow = (__nv_bfloat16 *)p;
+        }
+        c->use_tc = tc;
+    }
+    if (l.split_min != c->split_min || l.seg_len != c->seg_len || (c->split_min > 0 && !c->seg_part)) {
+        c->split_min = l.split_min;
+        c->seg_len = l.seg_len;
+        if ((s = build_split(c)) != ALS_OK) return s;
+    }
+    destroy_graphs(c);  // the captured iterations hold the old launch shapes
+    return ALS_OK;
+}
+
+bool launch_valid(const als_ctx *c, const als_launch &l) {
+    if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
+        l.seg_len < 32)
+        return false;
+    if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
+    if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" als_status als_get_launch(als_ctx *c, als_launch *out) {
+    if (!c || !out) { als_set_error("als_get_launch: bad argument"); return ALS_EINVAL; }
+    fill_launch(c, out);
+    return ALS_OK;
+}
+
+extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
+    if (!c || !in || !launch_valid(c, *in)) {
+        als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
+                      "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form)");
+        return ALS_EINVAL;
+    }
+    return apply_launch(c, *in);
+}
+
+extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *out) {
+    if (!c || reps < 1 || reps > 100) { als_set_error("als_autotune: bad argument"); return ALS_EINVAL; }
+    als_status s = load_degrees(c);
+    if (s != ALS_OK) return s;
+    void *scratch = c->tmpvec;  // n_u + n_m rows of ld doubles: holds any result vector
+    als_tune_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    als_launch cur;
+    fill_launch(c, &cur);
+    auto passes = [&]() -> als_status {
+        als_status st = grad_into(c, c->X, scratch, c->Gbar, c->G[0]);
+        if (st != ALS_OK) return st;
+        return lscoef_into(c, c->X, c->P);
+    };
+    auto sweep = [&]() -> als_status { return sweep_into(c, c->X, scratch, nullptr); };
+    // time `fn` with `cand` applied; keep it in `cur` when faster than `best`
+    auto trial = [&](const als_launch &cand, bool pass, double &best) -> als_status {
+        if (!launch_valid(c, cand)) return ALS_OK;
+        als_status st = apply_launch(c, cand);
+        if (st != ALS_OK) return st;
+        double ms;
+        st = pass ? time_best_ms(c, reps, passes, &ms) : time_best_ms(c, reps, sweep, &ms);
+        if (st != ALS_OK) return st;
+        ++rep.candidates;
+        if (ms < best) {
+            best = ms;
+            cur = cand;
+        }
+        return apply_launch(c, cur);
+    };
+
+    // 1. passes: heavy-row threshold, then the grid cap
+    if ((s = time_best_ms(c, reps, passes, &rep.pass_ms_default)) != ALS_OK) return s;
+    double best = rep.pass_ms_default;
+    for (int h : {256, 512, 1024, 2048, 4096, 8192, 1 << 30}) {
+        als_launch cand = cur;
+        cand.heavy_min = h;
+        if ((s = trial(cand, true, best)) != ALS_OK) return s;
+    }
+    for (int g : {4, 8, 16, 32, 64}) {
+        als_launch cand = cur;
+        cand.grid_mult = g;
+        if ((s = trial(cand, true, best)) != ALS_OK) return s;
+    }
+    rep.pass_ms_tuned = best;
+
+    // 2. sweep: Gram path (mixed, 16 < n_f <= 64), heavy-row split, FMA degree bin
+    if ((s = time_best_ms(c, reps, sweep, &rep.sweep_ms_default)) != ALS_OK) return s;
+    best = rep.sweep_ms_default;
+    if (!c->f64 && c->cfg.gram_path == ALS_GRAM_AUTO && c->nf > 16 && c->nf <= 64) {
+        als_launch cand = cur;
+        cand.gram_path = cur.gram_path == ALS_GRAM_TC ? ALS_GRAM_FMA : ALS_GRAM_TC;
+        if ((s = trial(cand, false, best)) != ALS_OK) return s;
+    }
+    {
+        const int split_c[][2] = {{0, 2048}, {2048, 1024}, {2048, 2048}, {4096, 1024}, {4096, 2048},
+                                  {4096, 4096}, {8192, 2048}, {8192, 4096}, {16384, 4096}};
+        for (const auto &sc : split_c) {
+            als_launch cand = cur;
+            cand.split_min = sc[0];
+            cand.seg_len = sc[1];
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+    }
+    if (c->nf <= 32 && cur.gram_path == ALS_GRAM_FMA) {
+        for (int b : {0, 16384, 4096, 1024, 256}) {
+            als_launch cand = cur;
+            cand.sweep_bin_min = b;
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+    }
+    rep.sweep_ms_tuned = best;
+    if ((s = apply_launch(c, cur)) != ALS_OK) return s;
+    rep.chosen = cur;
+    if (out) *out = rep;
+    return ALS_OK;
 }

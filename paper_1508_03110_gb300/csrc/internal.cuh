@@ -13,7 +13,7 @@
 
 #define ALS_MAX_NF 128
 #define ALS_TC_LD 128          // bf16 shadow row length used by the tcgen05 Gram
-#define ALS_HEAVY_MIN 2048     // rows at least this long get a whole CTA in the passes
+#define ALS_HEAVY_MIN 512      // rows at least this long get a whole CTA in the passes (default)
 
 // Slots of the device scalar block (double S[]).
 enum {
@@ -55,6 +55,8 @@ struct als_ctx {
     int dev = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side_stream = nullptr;   // split heavy rows run here, beside the light rows
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t allocated = 0;
     std::vector<DevAlloc> allocs;
 
@@ -90,6 +92,28 @@ struct als_ctx {
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};   // kernel nodes per captured iteration
+
+    // launch shapes (defaults, or chosen by als_autotune)
+    int heavy_min = ALS_HEAVY_MIN;     // rows with >= this many ratings: a CTA each in the passes
+    int grid_mult = 32;                // pass grids: at most grid_mult x sm_count CTAs
+    int sweep_bin_min = 0;             // FMA sweep, n_f <= 32: rows with >= this many ratings use a CTA (0: none)
+    int64_t sweep_big[2] = {0, 0};     // ... their count per side (a prefix of the degree order)
+    std::vector<int32_t> h_deg[2];     // degrees in degree order (host), filled on first use
+    std::vector<int64_t> h_beg[2];     // first rating of each row, in degree order (host)
+
+    // heavy rows split into segments (a prefix of each side's degree order)
+    int split_min = 4096;              // rows with >= this many ratings are split
+    int seg_len = 2048;                // ratings per segment
+    int64_t nsplit[2] = {0, 0};        // split rows per side
+    int64_t nseg[2] = {0, 0};          // segments per side
+    int32_t *seg_row[2] = {nullptr, nullptr};
+    int64_t *seg_beg[2] = {nullptr, nullptr};
+    int32_t *seg_len_d[2] = {nullptr, nullptr};
+    int32_t *hseg_off[2] = {nullptr, nullptr};   // [nsplit + 1] first segment of each split row
+    void *seg_part = nullptr;          // partials: max nseg x seg_stride (element size esz)
+    int64_t seg_stride = 0;
+    float *hfac = nullptr;             // mixed: factored matrices of the split rows, n_f x (n_f + 1) each
+    int32_t *hflag = nullptr;          // mixed: split rows that take another correction
 
     // batched problems (n_prob > 1): block-diagonal layout, per-problem scalars
     int n_prob = 1;
@@ -163,8 +187,25 @@ struct SweepArgs {
     int *notspd;
     int *timeout;           // set when a bounded device wait expired
     cudaStream_t stream = nullptr;  // launch stream (nullptr: the context's)
+    int64_t nbig = 0;       // FMA sweep: the first nbig rows of `order` get a CTA each
+    // segment mode (split heavy rows): "row" r is segment r, a slice
+    // [seg_beg[r], seg_beg[r] + seg_len[r]) of the ratings of row
+    // order[seg_row[r]]; the kernel writes that slice's partial Gram matrix
+    // (packed lower triangle, TRI = n_f (n_f + 1) / 2 values) and partial
+    // right-hand side (FP64 form) or residual at the row's current value
+    // (mixed form), n_f values, to seg_out + r * seg_stride, and solves nothing
+    const int32_t *seg_row = nullptr;
+    const int64_t *seg_beg = nullptr;
+    const int32_t *seg_len = nullptr;
+    void *seg_out = nullptr;
+    int64_t seg_stride = 0;
 };
 als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
+// heavy rows split across CTAs (sweep_split.cu): segment lists and buffers
+// for the current split_min / seg_len, then the split part of a half sweep
+als_status load_degrees(als_ctx *c);
+als_status build_split(als_ctx *c);
+als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side);
 // BF16 hi/lo shadow of F (rows x ld) into dst (nullptr: the context's shadow)
 als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst = nullptr,
                           cudaStream_t stream = nullptr);

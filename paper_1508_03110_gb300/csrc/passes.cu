@@ -644,7 +644,7 @@ __global__ void k_convert(TD *__restrict__ dst, const TS *__restrict__ src, int6
 
 inline unsigned grid_for(als_ctx *c, int64_t n, int threads) {
     const int64_t want = (n + threads - 1) / threads;
-    const int64_t cap = (int64_t)c->sm_count * 8;
+    const int64_t cap = (int64_t)c->sm_count * c->grid_mult;
     return (unsigned)std::max<int64_t>(1, std::min(want, cap));
 }
 
@@ -668,7 +668,7 @@ als_status grad_launch(als_ctx *c, const PassArgs &a, bool heavy) {
     } else {
         const int64_t groups_per_block = 256 / LPR;
         const int64_t want = (a.nrows + groups_per_block - 1) / groups_per_block;
-        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * 8));
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * c->grid_mult));
         k_grad<T, LPR><<<g, 256, 0, c->stream>>>(a);
     }
     ALS_CUDA_TRY(cudaGetLastError());
@@ -684,7 +684,7 @@ als_status lscoef_launch(als_ctx *c, const PassArgs &a, int kind) {  // 0 rows, 
     } else {
         const int64_t groups_per_block = 256 / LPR;
         const int64_t want = (a.nrows + groups_per_block - 1) / groups_per_block;
-        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * 8));
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * c->grid_mult));
         if (kind == 0) k_lscoef<T, LPR, HAS_P><<<g, 256, 0, c->stream>>>(a);
         else k_lscoef_reg<T, LPR, HAS_P><<<g, 256, 0, c->stream>>>(a);
     }

@@ -76,9 +76,10 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
     const int NT = nf * (nf + 1) / 2;
 
     for (int64_t r = (int64_t)blockIdx.x * G + g; r < a.nrows; r += (int64_t)gridDim.x * G) {
-        const int64_t row = a.order ? a.order[r] : r;
-        const int64_t beg = a.ptr[row];
-        const int n = (int)(a.ptr[row + 1] - beg);
+        const bool seg = a.seg_out != nullptr;  // a slice of a split row: partials only
+        const int64_t row = seg ? a.order[a.seg_row[r]] : (a.order ? a.order[r] : r);
+        const int64_t beg = seg ? a.seg_beg[r] : a.ptr[row];
+        const int n = seg ? a.seg_len[r] : (int)(a.ptr[row + 1] - beg);
         const T *xi = a.Xin ? reinterpret_cast<const T *>(a.Xin) + row * a.ld : nullptr;
         T *xo = reinterpret_cast<T *>(a.Xout) + row * a.ld;
         T *gb = a.Gbar ? reinterpret_cast<T *>(a.Gbar) + row * a.ld : nullptr;
@@ -89,12 +90,25 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
             T acc[MAXE];
 #pragma unroll
             for (int q = 0; q < MAXE; ++q) acc[q] = T(0);
-            T vacc = T(0);
+            T vacc = T(0), vcmp = T(0);
+            if (WARM && seg) {  // the slice's residual is taken at the row's current value
+                for (int k = t; k < nf; k += TPR) u[k] = xi ? xi[k] : T(0);
+            }
             for (int c0 = 0; c0 < n; c0 += CH) {
                 const int cn = min(CH, n - c0);
                 sw_gsync<TPR>();
                 stage_chunk<T, TPR>(a, F, beg + c0, cn, Fc, rc, ldA, t);
                 sw_gsync<TPR>();
+                if (WARM && seg) {
+                    for (int c = t; c < cn; c += TPR) {
+                        T d = T(0);
+                        for (int k = 0; k < nf; ++k) d = fma(Fc[c * ldA + k], u[k], d);
+                        err[c] = rc[c] - d;
+                    }
+                    sw_gsync<TPR>();
+                    if (t < nf)
+                        for (int c = 0; c < cn; ++c) kadd(vacc, vcmp, err[c] * Fc[c * ldA + t]);
+                }
                 int k, l;
                 tri_first(t, nf, k, l);
 #pragma unroll
@@ -114,6 +128,24 @@ __global__ void __launch_bounds__(128) k_sweep_fma(SweepArgs a) {
                 }
             }
             sw_gsync<TPR>();
+            if (seg) {
+                // the slice's partials: packed lower triangle (entry (l, k),
+                // k <= l, at l (l + 1) / 2 + k), then its right-hand side
+                // (FP64 form) or its residual at the current value (mixed)
+                T *po = reinterpret_cast<T *>(a.seg_out) + r * a.seg_stride;
+                int k, l;
+                tri_first(t, nf, k, l);
+#pragma unroll
+                for (int q = 0; q < MAXE; ++q) {
+                    if (t + q * TPR < NT) {
+                        po[l * (l + 1) / 2 + k] = acc[q];
+                        tri_next(TPR, nf, k, l);
+                    }
+                }
+                if (t < nf) po[NT + t] = WARM ? vacc - vcmp : vacc;
+                sw_gsync<TPR>();
+                continue;
+            }
             {
                 int k, l;
                 tri_first(t, nf, k, l);
@@ -221,12 +253,23 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a);  // sweep_tc.cu
 
 als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc) {
     if (tc && !f64) return launch_sweep_tc(c, a);
-    if (f64) {
-        if (a.nf <= 32) return sweep_launch<double, 32, 17, false>(c, a);
-        return sweep_launch<double, 128, 65, false>(c, a);
+    if (a.nf <= 32) {
+        // degree bin: the heaviest rows (a prefix of the degree order) get a
+        // CTA each, the rest a warp each
+        const int64_t nbig = a.order ? std::min<int64_t>(a.nbig, a.nrows) : 0;
+        als_status s = ALS_OK;
+        if (nbig > 0) {
+            SweepArgs b = a;
+            b.nrows = nbig;
+            s = f64 ? sweep_launch<double, 128, 65, false>(c, b) : sweep_launch<float, 128, 65, true>(c, b);
+            if (s != ALS_OK) return s;
+        }
+        SweepArgs r = a;
+        r.order = a.order ? a.order + nbig : nullptr;
+        r.nrows = a.nrows - nbig;
+        return f64 ? sweep_launch<double, 32, 17, false>(c, r) : sweep_launch<float, 32, 17, true>(c, r);
     }
-    if (a.nf <= 32) return sweep_launch<float, 32, 17, true>(c, a);
-    return sweep_launch<float, 128, 65, true>(c, a);
+    return f64 ? sweep_launch<double, 128, 65, false>(c, a) : sweep_launch<float, 128, 65, true>(c, a);
 }
 
 als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst,

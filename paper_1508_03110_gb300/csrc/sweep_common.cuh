@@ -87,6 +87,48 @@ __device__ void sw_trisolve(const T *A, int ldA, int nf, const T *diag, T *b, T 
     sw_gsync<TPR>();
 }
 
+__device__ __forceinline__ void ld4f(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+// acc += sum over q < 8 with 4 q < cnt of f_q (r_q - f_q . u), f_q the FP32
+// factor row of id ix[4 q] and r_q = vx[4 q]: the warp's share of the FP32
+// residual of the row's normal equations (lane = 4-wide slot of the row).
+// All eight rows are requested before any is used, so one gather latency
+// covers them.
+__device__ __forceinline__ void resid8(const float *F, int ld, const int32_t *ix, const float *vx, int64_t cnt,
+                                       const float (&uu)[4], int lane, bool act, float (&acc)[4],
+                                       float (&cmp)[4]) {
+    float f[8][4], d[8], r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool in = 4 * q < cnt;
+        const int64_t j = in ? ix[4 * q] : 0;
+        r[q] = in ? vx[4 * q] : 0.0f;
+        if (in && act) ld4f(F + j * ld + 4 * lane, f[q]);
+        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        d[q] = uu[0] * f[q][0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (4 * q < cnt) {
+            const float er = r[q] - d[q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
+        }
+    }
+}
+
 // Stopping test of the mixed form's refinement u <- u + Ahat^-1 (v - A u)
 // for a row with n ratings: true when rho(n) |dx| <= 2^-21 |u|, dx the last
 // correction.  A correction leaves at most rho |dx|, rho = |I - Ahat^-1 A|;

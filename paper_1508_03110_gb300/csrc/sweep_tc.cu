@@ -60,48 +60,6 @@ __host__ __device__ inline TcLayout tc_layout(int nf) {
     return L;
 }
 
-__device__ __forceinline__ void ld4f(const float *p, float (&v)[4]) {
-    const float4 q = *reinterpret_cast<const float4 *>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-
-// acc += sum over q < 8 with 4 q < cnt of f_q (r_q - f_q . u), f_q the FP32
-// factor row of id ix[4 q] and r_q = vx[4 q]: the warp's share of the FP32
-// residual of the row's normal equations (lane = 4-wide slot of the row).
-// All eight rows are requested before any is used, so one gather latency
-// covers them.
-__device__ __forceinline__ void resid8(const float *F, int ld, const int32_t *ix, const float *vx, int64_t cnt,
-                                       const float (&uu)[4], int lane, bool act, float (&acc)[4],
-                                       float (&cmp)[4]) {
-    float f[8][4], d[8], r[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const bool in = 4 * q < cnt;
-        const int64_t j = in ? ix[4 * q] : 0;
-        r[q] = in ? vx[4 * q] : 0.0f;
-        if (in && act) ld4f(F + j * ld + 4 * lane, f[q]);
-        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        d[q] = uu[0] * f[q][0];
-#pragma unroll
-        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        if (4 * q < cnt) {
-            const float er = r[q] - d[q];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -138,9 +96,10 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
     bool bail = false;
 
     for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
-        const int64_t row = a.order ? a.order[r] : r;
-        const int64_t beg = a.ptr[row];
-        const int n = (int)(a.ptr[row + 1] - beg);
+        const bool seg = a.seg_out != nullptr;  // a slice of a split row: partials only
+        const int64_t row = seg ? a.order[a.seg_row[r]] : (a.order ? a.order[r] : r);
+        const int64_t beg = seg ? a.seg_beg[r] : a.ptr[row];
+        const int n = seg ? a.seg_len[r] : (int)(a.ptr[row + 1] - beg);
         const float *xi = a.Xin ? reinterpret_cast<const float *>(a.Xin) + row * a.ld : nullptr;
         float *xo = reinterpret_cast<float *>(a.Xout) + row * a.ld;
         float *gb = a.Gbar ? reinterpret_cast<float *>(a.Gbar) + row * a.ld : nullptr;
@@ -263,6 +222,22 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             }
             tc_fence_before();
             __syncthreads();
+            if (seg) {
+                // the slice's partials: packed lower triangle of the symmetric
+                // part of D (row m at m (m + 1) / 2), then its residual at u0
+                float *po = reinterpret_cast<float *>(a.seg_out) + r * a.seg_stride;
+                const int tri = nf * (nf + 1) / 2;
+                for (int e = t; e < tri; e += TC_THREADS) {
+                    int m = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                    while ((m + 1) * (m + 2) / 2 <= e) ++m;
+                    while (m * (m + 1) / 2 > e) --m;
+                    const int cc = e - m * (m + 1) / 2;
+                    po[e] = 0.5f * (A[m * ldA + cc] + A[cc * ldA + m]);
+                }
+                if (t < nf) po[tri + t] = (part[t] + part[128 + t]) + (part[256 + t] + part[384 + t]);
+                __syncthreads();
+                continue;
+            }
             // symmetric part of D, lower triangle, plus lambda n I; the first
             // residual v1 = r0 - lambda n u0 (fixed order over the warps)
             if (t < nf) {
