@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--gram", default="auto", choices=["auto", "fma", "tc"])
     ap.add_argument("--refine", type=int, default=2, help="maximum refinement corrections per row")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default shapes)")
+    ap.add_argument("--launch", default="", help="launch shapes key=value,... (als_set_launch; skips tuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
@@ -383,6 +385,15 @@ def main():
     kw = dict(precision=args.precision, refine_steps=args.refine, gram_path=args.gram, stream=stream)
     m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, **kw)
     m.set_x(x0)
+    # launch shapes: given, or chosen by the autotuner on this workload (one-time
+    # setup like the ratings builder, outside the timed region)
+    tune = None
+    if args.launch:
+        m.set_launch(**{k: (v if k == "gram_path" and not v.isdigit() else int(v))
+                        for k, v in (kv.split("=") for kv in args.launch.split(","))})
+    elif not args.no_tune:
+        tune = m.autotune(reps=2)
+    launch = m.get_launch()
     m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
@@ -391,10 +402,12 @@ def main():
     time.sleep(0.3)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     info = m.run(args.steps, 0.0, check_every=args.steps)
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     t = e0.elapsed_time(e1) / 1e3
     barrier()
     clocks = sampler.stop()
@@ -416,7 +429,7 @@ def main():
     s1.synchronize()
     t_sweep = s0.elapsed_time(s1) / 1e3 / reps
     fl = sweep_flops(r, r.n_f, args.refine, args.precision)
-    use_tc = args.precision == "mixed" and r.n_f > 32 and args.gram != "fma"
+    use_tc = args.precision == "mixed" and launch["gram_path"] == 2
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     if use_tc:
@@ -443,7 +456,8 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "k_sweep_tc (fused gather, tensor-core Gram, Cholesky, solves)" if use_tc
                 else "k_sweep_fma (fused Gram, Cholesky, solves)",
-                "peak_source": peak_note, "sweep_ms": t_sweep * 1e3, "launches_per_sweep": 2}
+                "peak_source": peak_note, "sweep_ms": t_sweep * 1e3,
+                "what": "one sweep P(x): every launch of both half sweeps (split heavy rows included)"}
     if alu_part:
         roofline["alu_part"] = alu_part
     m.close()
@@ -496,8 +510,12 @@ def main():
                "dtype": "f64" if args.precision == "fp64" else ("bf16+f32" if use_tc else "f32"),
                "data": "synthetic",
                "config": {"workload": workload_name(args, r), "precision": args.precision,
-                          "gram": args.gram, "refine_steps": args.refine,
-                          "l2": "inputs larger than L2 (ratings stored twice: 320 MB; vectors 66 MB each)"},
+                          "gram": args.gram, "refine_steps": args.refine, "launch": launch,
+                          "autotune": None if tune is None else
+                          {k: tune[k] for k in ("candidates", "pass_ms_default", "pass_ms_tuned",
+                                                "sweep_ms_default", "sweep_ms_tuned")},
+                          "l2": (f"inputs larger than L2 (ratings stored twice: {r.nnz * 16 / 1e6:.0f} MB; "
+                                 f"vectors {(r.n_u + r.n_m) * ((r.n_f + 3) // 4 * 4) * (8 if args.precision == 'fp64' else 4) / 1e6:.0f} MB each)")},
                "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "e2e": e2e,
                "cpu_baseline": cpu, "final_gnorm_rel": info["gnorm"] / info["gnorm0"], **extra}
         print(json.dumps(out), flush=True)

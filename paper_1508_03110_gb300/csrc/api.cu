@@ -115,7 +115,6 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.order = side ? c->morder : c->uorder;
     a.nrows = side ? c->n_m : c->n_u;
     a.F = F;
-    a.Fbf = c->shadow;
     a.Xin = Xin;
     a.Xout = Xout;
     a.Gbar = Gbar;
@@ -126,10 +125,6 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.notspd = c->dflags;
     a.timeout = c->dflags + 7;
     a.nbig = c->sweep_big[side];
-    if (c->use_tc) {
-        als_status s = launch_to_bf16(c, F, side ? c->n_u : c->n_m, c->f64);
-        if (s != ALS_OK) return s;
-    }
     const int64_t H = c->nsplit[side];
     if (H == 0) return launch_sweep(c, a, c->f64, c->use_tc);
     // the heaviest rows, split across CTAs, on the side stream; the rest, one
@@ -529,10 +524,6 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
         c->h_segu = bs->segu;
         c->h_segm = bs->segm;
     }
-    if (c->use_tc) {
-        c->shadow_rows = std::max(n_u, n_m);
-        ALLOC(c->shadow, (size_t)c->shadow_rows * 2 * ALS_TC_LD * sizeof(__nv_bfloat16));
-    }
 #undef ALLOC
     if (cudaMallocHost(&c->hS, (size_t)c->n_prob * S_COUNT * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->hflags, 16 * sizeof(int)) != cudaSuccess) {
@@ -898,7 +889,6 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     a.order = nullptr;
     a.nrows = n_req;
     a.F = mblk(c, c->X);
-    a.Fbf = c->shadow;
     a.Xin = nullptr;
     a.Xout = dout;
     a.Gbar = nullptr;
@@ -908,10 +898,6 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     a.refine = c->cfg.refine_steps + 1;  // cold start: one more correction
     a.notspd = c->dflags + 5;
     a.timeout = c->dflags + 7;
-    if (c->use_tc) {
-        s = launch_to_bf16(c, a.F, c->n_m, c->f64);
-        if (s != ALS_OK) { cleanup(); return s; }
-    }
     s = launch_sweep(c, a, c->f64, c->use_tc);
     if (s != ALS_OK) { cleanup(); return s; }
     s = launch_convert_out(c, c->tmpvec, dout, n_req, dtype, c->nf);
@@ -1030,15 +1016,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
     c->sweep_big[0] = l.sweep_bin_min > 0 ? rows_at_least(c, 0, l.sweep_bin_min) : 0;
     c->sweep_big[1] = l.sweep_bin_min > 0 ? rows_at_least(c, 1, l.sweep_bin_min) : 0;
     if (!c->f64) {
-        const bool tc = l.gram_path == ALS_GRAM_TC;
-        if (tc && !c->shadow) {
-            c->shadow_rows = std::max(c->n_u, c->n_m);
-            void *p = nullptr;
-            if ((s = ctx_alloc(c, &p, (size_t)c->shadow_rows * 2 * ALS_TC_LD * sizeof(__nv_bfloat16))) != ALS_OK)
-                return s;
-            c->shadow = (__nv_bfloat16 *)p;
-        }
-        c->use_tc = tc;
+        c->use_tc = l.gram_path == ALS_GRAM_TC;
     }
     if (l.split_min != c->split_min || l.seg_len != c->seg_len || (c->split_min > 0 && !c->seg_part)) {
         c->split_min = l.split_min;

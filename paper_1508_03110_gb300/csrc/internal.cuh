@@ -12,7 +12,7 @@
 #include "als.h"
 
 #define ALS_MAX_NF 128
-#define ALS_TC_LD 128          // bf16 shadow row length used by the tcgen05 Gram
+#define ALS_TC_LD 128          // widest n_f of the tcgen05 Gram (one 128-row MMA tile)
 #define ALS_HEAVY_MIN 512      // rows at least this long get a whole CTA in the passes (default)
 
 // Slots of the device scalar block (double S[]).
@@ -73,8 +73,6 @@ struct als_ctx {
     void *X = nullptr, *Xbar = nullptr, *Gbar = nullptr, *G[2] = {nullptr, nullptr}, *P = nullptr;
     int gcur = 0;
     void *tmpvec = nullptr;          // staging for user-supplied vectors
-    __nv_bfloat16 *shadow = nullptr; // bf16 copy of the fixed side (tcgen05 Gram)
-    int64_t shadow_rows = 0;
 
     // deterministic reductions
     double *rowterm = nullptr;   // 5 x (n_u + n_m)
@@ -177,7 +175,6 @@ struct SweepArgs {
     const int32_t *order;   // rows to process, in this order (nullptr = 0..nrows-1)
     int64_t nrows;
     const void *F;          // fixed-side factors, ld-strided (T)
-    const __nv_bfloat16 *Fbf;  // bf16 shadow of F (ALS_TC_LD-strided), tcgen05 path
     const void *Xin;        // current rows (warm start; Gbar = Xin - Xout); may be null
     void *Xout;             // solved rows
     void *Gbar;             // optional Gbar rows
@@ -206,9 +203,6 @@ als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
 als_status load_degrees(als_ctx *c);
 als_status build_split(als_ctx *c);
 als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side);
-// BF16 hi/lo shadow of F (rows x ld) into dst (nullptr: the context's shadow)
-als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst = nullptr,
-                          cudaStream_t stream = nullptr);
 
 // ---------------------------------------------------------------------------
 // passes (passes.cu)

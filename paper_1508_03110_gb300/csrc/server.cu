@@ -83,7 +83,6 @@ struct als_server {
     als_ctx *model = nullptr;
     als_server_config cfg;
     cudaStream_t stream = nullptr;
-    __nv_bfloat16 *shadow = nullptr;
     int *dflags = nullptr;
     std::vector<Slot> slots;
     std::mutex mu;
@@ -156,7 +155,6 @@ bool launch_batch(als_server *s, Slot &sl) {
     a.order = nullptr;
     a.nrows = nreq;
     a.F = (const char *)c->X + (size_t)c->n_u * c->ld * c->esz;
-    a.Fbf = s->shadow;
     a.Xin = nullptr;
     a.Xout = sl.dout;
     a.Gbar = nullptr;
@@ -351,7 +349,7 @@ extern "C" als_status als_server_create(als_ctx *model, const als_server_config 
         return fail(ALS_ECUDA, "stream creation failed");
     }
     const size_t ob = (size_t)cfg.max_batch * model->ld * model->esz;
-    // the model's pending work (factors, shadow) must be finished before the
+    // the model's pending work (its factors) must be finished before the
     // server's stream reads M
     if (cudaStreamSynchronize(model->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -361,15 +359,6 @@ extern "C" als_status als_server_create(als_ctx *model, const als_server_config 
         cudaMemsetAsync(s->dflags, 0, 2 * (size_t)cfg.slots * sizeof(int), s->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(ALS_ENOMEM, "device allocation failed");
-    }
-    if (model->use_tc) {
-        if (cudaMalloc(&s->shadow, (size_t)model->n_m * 2 * ALS_TC_LD * sizeof(__nv_bfloat16)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ALS_ENOMEM, "device allocation failed");
-        }
-        const void *M = (const char *)model->X + (size_t)model->n_u * model->ld * model->esz;
-        if (launch_to_bf16(model, M, model->n_m, model->f64, s->shadow, s->stream) != ALS_OK)
-            return fail(ALS_ECUDA, "shadow conversion failed");
     }
     s->slots.resize(cfg.slots);
     for (size_t i = 0; i < s->slots.size(); ++i) {
@@ -544,7 +533,6 @@ extern "C" void als_server_destroy(als_server *s) {
         if (kv.second->ctx) als_destroy(kv.second->ctx);
         delete kv.second;
     }
-    if (s->shadow) cudaFree(s->shadow);
     if (s->dflags) cudaFree(s->dflags);
     if (s->stream) cudaStreamDestroy(s->stream);
     cudaGetLastError();

@@ -230,23 +230,6 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
     return ALS_OK;
 }
 
-// Two-term BF16 shadow of the fixed side for the tensor-core Gram: row r is
-// [hi(128) | lo2(128)] with hi = bf16(f), lo2 = bf16(2 (f - hi)); f - hi is
-// exact in FP32 and the factor 2 is exact, so f = hi + lo2 / 2 to ~2^-17.
-template <typename T>
-__global__ void k_to_bf16(const T *__restrict__ F, int64_t rows, int ld, __nv_bfloat16 *__restrict__ out) {
-    const int64_t n = rows * ALS_TC_LD;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / ALS_TC_LD;
-        const int k = (int)(i - r * ALS_TC_LD);
-        const float f = k < ld ? (float)F[r * ld + k] : 0.0f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-        const float lo2 = 2.0f * (f - __bfloat162float(hi));
-        out[r * (2 * ALS_TC_LD) + k] = hi;
-        out[r * (2 * ALS_TC_LD) + ALS_TC_LD + k] = __float2bfloat16_rn(lo2);
-    }
-}
-
 }  // namespace
 
 als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a);  // sweep_tc.cu
@@ -272,15 +255,3 @@ als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc) {
     return f64 ? sweep_launch<double, 128, 65, false>(c, a) : sweep_launch<float, 128, 65, true>(c, a);
 }
 
-als_status launch_to_bf16(als_ctx *c, const void *F, int64_t rows, bool f64, __nv_bfloat16 *dst,
-                          cudaStream_t stream) {
-    if (rows <= 0) return ALS_OK;
-    const int64_t n = rows * ALS_TC_LD;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 8));
-    __nv_bfloat16 *out = dst ? dst : c->shadow;
-    cudaStream_t st = stream ? stream : c->stream;
-    if (f64) k_to_bf16<double><<<g, 256, 0, st>>>((const double *)F, rows, c->ld, out);
-    else k_to_bf16<float><<<g, 256, 0, st>>>((const float *)F, rows, c->ld, out);
-    ALS_CUDA_TRY(cudaGetLastError());
-    return ALS_OK;
-}

@@ -2,28 +2,29 @@
 // tensor cores (tcgen05, sm_103a).
 //
 // For each row i (one CTA of 4 warps per row, 4 CTAs per SM), with the fixed
-// side F kept in a BF16 shadow of 128 columns:
-//   1. gather: each factor row is held as two BF16 rows, hi = bf16(f) and
-//      lo2 = bf16(2 (f - hi)); the rows of the row's ratings, 32 per chunk,
-//      are copied with cp.async into two 128-byte-swizzled, MN-major shared
-//      tiles H and L (rating k of the chunk is K index k, the factor index is
-//      the M/N index);
+// side F (FP32 factor rows):
+//   1. gather: the row's ratings are taken 32 per chunk, a warp 8 of them;
+//      each rating's factor row f is read once, into registers, and split
+//      into hi = bf16(f) and lo2 = bf16(2 (f - hi)), stored into two
+//      128-byte-swizzled, MN-major shared tiles H and L (rating k of the chunk
+//      is K index k, the factor index is the M/N index); the same FP32 values
+//      give the chunk's part of the first residual sum_e f_e (r_e - f_e . u0)
+//      at the current row u0 = x_i;
 //   2. Gram: one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
 //      M = 128, N = round_up(n_f, 16), K = 16 per instruction): D += H H^T
 //      and D += H L^T, so D = sum_e hi_e (hi_e + 2 lo_e)^T accumulates in
 //      TMEM; its symmetric part is sum_e (hi hi^T + hi lo^T + lo hi^T), the
 //      Gram matrix with ~2^-17 relative error (the lo lo^T term is dropped).
-//      Chunks are double buffered; tcgen05.commit on an mbarrier releases a
-//      stage;
+//      Two stages: while the MMAs of one chunk run, the next chunk's rows are
+//      read and split; tcgen05.commit on an mbarrier releases a stage;
 //   3. tcgen05.ld moves D into FP32 shared memory (row m of D is TMEM lane
 //      m), A = (D + D^T)/2 + lambda n_i I;
 //   4. blocked Cholesky of A (inverted diagonal blocks) and the refinement of
-//      the ALS solve from the current row u0 = x_i: res = sum_e f_e (r_e -
-//      f_e . u) - lambda n_i u in FP32 from the FP32 factors, u <- u +
-//      A^{-1} res.  The first residual (at u0) is gathered inside the Gram
-//      loop, while the chunk's copies and MMAs are in flight.
+//      the ALS solve from u0: u <- u + A^{-1} res, res = sum_e f_e (r_e -
+//      f_e . u) - lambda n_i u in FP32 from the FP32 factors (the first
+//      residual comes from step 1).
 // Every mbarrier wait is bounded (%globaltimer): on expiry the CTA records a
-// timeout, waits for its copies, frees its TMEM and returns.
+// timeout, frees its TMEM and returns.
 #include "internal.cuh"
 #include "sweep_common.cuh"
 #include "tc_ptx.cuh"
@@ -41,15 +42,14 @@ constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int TMEM_COLS = 128;
 
 struct TcLayout {
-    int ring, meta, A, vec, mbar, holder, total;
+    int ring, A, vec, mbar, holder, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int nf) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
-    L.meta = NSTAGE * STAGE_BYTES;  // per stage: the chunk's ids, then its ratings
-    int big = L.meta + NSTAGE * KCH * 8;
+    int big = NSTAGE * STAGE_BYTES;
     const int a_bytes = nf * (nf + 1) * 4;
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
@@ -74,8 +74,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
     float *colk = vec, *v1 = vec + 128, *v2 = vec + 256, *u = vec + 384, *diag = vec + 512;
     float *part = vec + 640;   // residual partials (residual phase)
     float *work = vec + 640;   // Cholesky panel scratch (factorisation phase)
-    int32_t *meta_i = reinterpret_cast<int32_t *>(base + L.meta);          // [NSTAGE][KCH]
-    float *meta_v = reinterpret_cast<float *>(base + L.meta + NSTAGE * KCH * 4);
     const uint32_t mbar[2] = {sbase + L.mbar, sbase + L.mbar + 8};
     uint32_t *holder = reinterpret_cast<uint32_t *>(base + L.holder);
 
@@ -91,7 +89,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
     const uint32_t tmem = *holder;
     const uint32_t idesc = idesc_bf16_f32_mn((uint32_t)ntc);
     const float *F = reinterpret_cast<const float *>(a.F);
-    const __nv_bfloat16 *Fb = a.Fbf;
     uint32_t phase[2] = {0u, 0u};
     bool bail = false;
 
@@ -117,65 +114,89 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             //      while the chunk's copies and MMAs are in flight -------------
             const int nch = (n + KCH - 1) / KCH;
             int pend[2] = {0, 0};
-            // ids and ratings of the next chunk to gather: thread t copies
-            // ratings k0 + 8 j (j < 4) of a chunk, k0 = (t / 16) % 8
-            const int k0 = (t >> 4) & 7;
-            int32_t pj[4];
-            float pv[4];
-            auto prefetch = [&](int ch) {
+            // ids and ratings of this warp's ratings k = warp + 4 q (q < 8) of
+            // the next chunk, fetched one chunk ahead
+            int32_t nj[8];
+            float nr[8];
+            auto fetch = [&](int ch) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int64_t e = beg + (int64_t)ch * KCH + k0 + 8 * j;
+                for (int q = 0; q < 8; ++q) {
+                    const int64_t e = beg + (int64_t)ch * KCH + warp + 4 * q;
                     const bool in = ch < nch && e < beg + n;
-                    pj[j] = in ? a.idx[e] : -1;
-                    pv[j] = in ? a.val[e] : 0.0f;
+                    nj[q] = in ? a.idx[e] : -1;
+                    nr[q] = in ? a.val[e] : 0.0f;
                 }
             };
-            auto gather = [&](int st) {
-                const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
-#pragma unroll
-                for (int i = 0; i < (2 * KCH * 16) / TC_THREADS; ++i) {
-                    const int p = t + TC_THREADS * i;
-                    const int part_ = p >> 9, k = (p >> 4) & (KCH - 1), q = p & 15;
-                    const uint32_t dst = stage + part_ * TILE_BYTES + (k >> 3) * SBO + (q >> 3) * LBO + (k & 7) * 128 +
-                                         ((uint32_t)((q & 7) ^ (k & 7)) << 4);
-                    const int32_t j = pj[i & 3];
-                    if (j >= 0) cp_async16(dst, Fb + (int64_t)j * (2 * ALS_TC_LD) + part_ * ALS_TC_LD + q * 8);
-                    else cp_async16_zero(dst, Fb);
-                }
-                cp_async_commit();
-                if ((t & 15) == 0) {  // the chunk's ids and ratings for its residual
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        meta_i[st * KCH + k0 + 8 * j] = pj[j];
-                        meta_v[st * KCH + k0 + 8 * j] = pv[j];
-                    }
-                }
-            };
-            prefetch(0);
-            gather(0);
-            prefetch(1);
-            __syncthreads();  // chunk 0's ids and ratings visible to every warp
+            fetch(0);
             for (int ch = 0; ch < nch; ++ch) {
                 const int st = ch & 1;
-                if (ch + 1 < nch) {
-                    const int sn = st ^ 1;
-                    if (pend[sn]) {  // the MMAs of chunk ch-1 still read stage sn
-                        const bool w = mbar_wait_bounded(mbar[sn], phase[sn], WAIT_NS);
-                        if (__syncthreads_or(!w)) { bail = true; break; }
-                        phase[sn] ^= 1u;
-                        pend[sn] = 0;
-                    }
-                    gather(sn);
-                    prefetch(ch + 2);
+                if (pend[st]) {  // the MMAs of chunk ch-2 still read stage st
+                    const bool w = mbar_wait_bounded(mbar[st], phase[st], WAIT_NS);
+                    if (__syncthreads_or(!w)) { bail = true; break; }
+                    phase[st] ^= 1u;
+                    pend[st] = 0;
                 }
+                int32_t cj[8];
+                float cr[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    cj[q] = nj[q];
+                    cr[q] = nr[q];
+                }
+                fetch(ch + 1);
+                // each factor row is read once, in FP32: it feeds the residual
+                // at u0 and, split into BF16 hi + lo, the operand tiles of stage st
                 {
-                    const int cnt = (n - ch * KCH < KCH) ? n - ch * KCH : KCH;
-                    resid8(F, a.ld, meta_i + st * KCH + warp, meta_v + st * KCH + warp, cnt - warp, uu, lane, act,
-                           acc, cmp);
+                    float f[8][4];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (cj[q] >= 0 && act) ld4f(F + (int64_t)cj[q] * a.ld + 4 * lane, f[q]);
+                        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
+                    }
+                    float d[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        d[q] = uu[0] * f[q][0];
+#pragma unroll
+                        for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (cj[q] >= 0) {
+                            const float er = cr[q] - d[q];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
+                        }
+                    }
+                    if (act) {
+                        const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int k = warp + 4 * q;   // K index (rating within the chunk)
+                            const int qq = lane >> 1;     // 16-byte column chunk: factors 8 qq .. 8 qq + 7
+                            const uint32_t off = (uint32_t)(k >> 3) * SBO + (uint32_t)(qq >> 3) * LBO +
+                                                 (uint32_t)(k & 7) * 128 + ((uint32_t)((qq & 7) ^ (k & 7)) << 4) +
+                                                 (uint32_t)(lane & 1) * 8;
+                            uint32_t hw[2], lw[2];
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const __nv_bfloat16 h0 = __float2bfloat16_rn(f[q][2 * i]);
+                                const __nv_bfloat16 h1 = __float2bfloat16_rn(f[q][2 * i + 1]);
+                                const __nv_bfloat16 l0 = __float2bfloat16_rn(2.0f * (f[q][2 * i] - __bfloat162float(h0)));
+                                const __nv_bfloat16 l1 =
+                                    __float2bfloat16_rn(2.0f * (f[q][2 * i + 1] - __bfloat162float(h1)));
+                                hw[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                                lw[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                            }
+                            st_shared_v2(stage + off, hw[0], hw[1]);
+                            st_shared_v2(stage + TILE_BYTES + off, lw[0], lw[1]);
+                        }
+                    }
                 }
-                if (ch + 1 < nch) cp_async_wait<1>();
-                else cp_async_wait<0>();
                 fence_proxy_async_smem();
                 __syncthreads();
                 if (t == 0) {
@@ -280,8 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
         }
         __syncthreads();
     }
-    // ---- teardown: no copies in flight, TMEM returned -------------------------
-    cp_async_wait_all();
+    // ---- teardown: TMEM returned ----------------------------------------------
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -43,6 +43,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
 }
 
 // ---- cp.async (16 B, L2 only) -------------------------------------------------
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
