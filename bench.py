@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving", "batched"])
+    ap.add_argument("--n-prob", type=int, default=64, help="batched: number of problems")
     ap.add_argument("--rates", default="1e3,1e4,1e5", help="serving: Poisson arrival rates (req/s)")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--jobs", type=int, default=2, help="serving: factorisation jobs per rate")
@@ -215,6 +216,58 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """Many independent problems of uneven size and different n_f (round robin
+    over 10, 20, 50, 100; ratings log-uniform in [1e4, 1e7]; density 0.1-5%):
+    one batched context per n_f, all problems of a context in the same
+    launches, the contexts iterated together on their own streams (each
+    iteration a captured graph per context).  Reports ratings x iterations per
+    second over all problems, against running the contexts one after another,
+    and the time until every problem reaches |g| <= 1e-4 |g_0|."""
+    import torch
+    import synth
+    from paper_1508_03110_gb300 import ALSGroup
+
+    t0 = time.perf_counter()
+    probs, n_fs = synth.c4_problems(args.n_prob, seed=4)
+    gen_s = time.perf_counter() - t0
+    xs = [synth.init_factors(p[0], p[1], nf, 100 + q) for q, (p, nf) in enumerate(zip(probs, n_fs))]
+    nnz = sum(len(p[4]) for p in probs)
+    out = {"mode": "batched", "workload": f"{len(probs)} synthetic problems, ratings log-uniform [1e4, 1e7] "
+           f"(total {nnz:,}), density 0.1-5%, n_f round robin {list(synth.C4_NF)}, lambda 0.05, mixed",
+           "generation_s": gen_s}
+    steps = args.steps
+    with ALSGroup(probs, n_fs, 0.05, precision="mixed") as g:
+        g.set_x(xs)
+        out["launch"] = {nf: {k: r[k] for k in ("heavy_min", "split_min", "seg_len", "gram_path")}
+                         for nf, r in g.autotune_reports.items()}
+        g.run(args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = g.run(steps, check_every=steps)
+        torch.cuda.synchronize()
+        t_group = time.perf_counter() - t0
+        # the same contexts one after another (each waits for the previous)
+        t0 = time.perf_counter()
+        for b in g.batches.values():
+            b.run(steps, 0.0, check_every=steps)
+            b.sync()
+        t_seq = time.perf_counter() - t0
+    with ALSGroup(probs, n_fs, 0.05, precision="mixed") as g:
+        g.set_x(xs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv = g.run(2000, rel_tol=1e-4, check_every=10)
+        t_tol = time.perf_counter() - t0
+        worst = max(i["gnorm"] / i["gnorm0"] for i in g.infos())
+    out.update({"ratings": nnz, "iterations": steps, "ms_per_iter_group": t_group / steps * 1e3,
+                "ratings_iter_per_s_group": nnz * steps / t_group,
+                "ms_per_iter_sequential": t_seq / steps * 1e3,
+                "kernels_per_iter": info["kernels"] / steps,
+                "s_to_1e-4": t_tol, "iters_to_1e-4": conv["iters"], "worst_rel_gnorm": worst})
+    print(json.dumps(out), flush=True)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -362,6 +415,9 @@ def main():
         return
     if args.mode == "serving":
         run_serving(args)
+        return
+    if args.mode == "batched":
+        run_batched(args)
         return
     import torch
     import synth

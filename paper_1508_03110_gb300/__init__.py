@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import (ALS_FP64, ALS_MIXED, ALS_LS_BACKTRACK, ALS_LS_EXACT, ALS_DT_F64, ALS_DT_F32,  # noqa: F401
                    ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC, ALSError, IterInfo)
 
-__all__ = ["ALS", "ALSBatch", "Server", "ALSError", "load", "info_dict", "make_config"]
+__all__ = ["ALS", "ALSBatch", "ALSGroup", "Server", "ALSError", "load", "info_dict", "make_config"]
 
 
 def load():
@@ -443,3 +443,69 @@ class Server:
         _lib.check(self.lib.als_server_stats(self.srv, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n),
                                              ctypes.byref(rps)), "als_server_stats")
         return {"p50_s": p50.value, "p99_s": p99.value, "completed": n.value, "requests_per_s": rps.value}
+
+
+class ALSGroup:
+    """A collection of independent problems with different n_f: one batched
+    context per n_f value (all its problems in the same launches), each on
+    its own CUDA stream, iterated together by als_group_run so that the
+    contexts' kernels overlap on the GPU.
+
+    problems: list of (n_u, n_m, rows, cols, vals) with local ids; n_fs: the
+    n_f of each problem."""
+
+    def __init__(self, problems, n_fs, lam, precision="mixed", autotune=True, **kw):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.order = {}
+        for q, nf in enumerate(n_fs):
+            self.order.setdefault(int(nf), []).append(q)
+        self.n_prob = len(problems)
+        self.streams = {nf: torch.cuda.Stream() for nf in self.order}
+        self.batches = {nf: ALSBatch([problems[q] for q in qs], nf, lam, precision=precision,
+                                     stream=self.streams[nf], **kw)
+                        for nf, qs in self.order.items()}
+        self.autotune_reports = {}
+        self._autotune = autotune
+
+    def close(self):
+        for b in self.batches.values():
+            b.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_x(self, xs):
+        """xs: the n_f-wide x_0 of every problem, in problem order."""
+        for nf, qs in self.order.items():
+            b = self.batches[nf]
+            b.set_x(b.join_x([xs[q] for q in qs]))
+        if self._autotune and not self.autotune_reports:
+            self.autotune_reports = {nf: b.autotune(reps=1) for nf, b in self.batches.items()}
+
+    def get_x(self):
+        out = [None] * self.n_prob
+        for nf, qs in self.order.items():
+            parts = self.batches[nf].split_x(self.batches[nf].get_x())
+            for q, x in zip(qs, parts):
+                out[q] = x
+        return out
+
+    def run(self, max_iter, rel_tol=0.0, check_every=10):
+        members = list(self.batches.values())
+        arr = (ctypes.c_void_p * len(members))(*[b.ctx.value for b in members])
+        infos = (IterInfo * len(members))()
+        done = ctypes.c_int32()
+        _lib.check(self.lib.als_group_run(arr, len(members), int(max_iter), float(rel_tol), int(check_every),
+                                          infos, ctypes.byref(done)), "als_group_run")
+        return {"iters": done.value, "kernels": sum(i.kernels for i in infos)}
+
+    def infos(self):
+        out = [None] * self.n_prob
+        for nf, qs in self.order.items():
+            for q, info in zip(qs, self.batches[nf].infos()):
+                out[q] = info
+        return out

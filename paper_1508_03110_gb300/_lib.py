@@ -100,6 +100,8 @@ SIGNATURES = {
     "als_get_launch": (_i32, [_vp, ctypes.POINTER(Launch)]),
     "als_set_launch": (_i32, [_vp, ctypes.POINTER(Launch)]),
     "als_autotune": (_i32, [_vp, _i32, ctypes.POINTER(TuneReport)]),
+    "als_group_run": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _dbl, _i32, ctypes.POINTER(IterInfo),
+                             ctypes.POINTER(_i32)]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
     "als_last_error": (ctypes.c_char_p, []),

@@ -1130,3 +1130,61 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
     if (out) *out = rep;
     return ALS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Groups of contexts (problems of different n_f): every member's captured
+// iteration is launched on the member's own stream, so the members' kernels
+// overlap on the GPU; the host only enqueues.
+
+extern "C" als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter, double rel_tol,
+                                    int32_t check_every, als_iter_info *last, int32_t *iters_done) {
+    if (!ctxs || n < 1 || max_iter < 0 || check_every < 1) {
+        als_set_error("als_group_run: bad argument");
+        return ALS_EINVAL;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ctxs[i]) { als_set_error("als_group_run: a member is NULL"); return ALS_EINVAL; }
+        for (int32_t j = 0; j < i; ++j) {
+            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) {
+                als_set_error("als_group_run: members must be distinct contexts on distinct streams");
+                return ALS_EINVAL;
+            }
+        }
+    }
+    als_status s;
+    for (int32_t i = 0; i < n; ++i) {
+        als_ctx *c = ctxs[i];
+        if (!c->ncg_ready && (s = ncg_init(c)) != ALS_OK) return s;
+        if ((s = capture_graphs(c)) != ALS_OK) return s;
+    }
+    std::vector<int64_t> nk(n, 0);
+    int32_t done = 0;
+    bool converged = false;
+    while (done < max_iter && !converged) {
+        for (int32_t i = 0; i < n; ++i) {
+            als_ctx *c = ctxs[i];
+            ALS_CUDA_TRY(cudaGraphLaunch(c->graph[c->gcur], c->stream));
+            nk[i] += c->graph_kernels[c->gcur];
+            c->gcur ^= 1;
+            c->k += 1;
+        }
+        ++done;
+        if (done % check_every == 0 || done == max_iter) {
+            double worst = 0.0;
+            for (int32_t i = 0; i < n; ++i) {
+                if ((s = read_scalars(ctxs[i])) != ALS_OK) return s;
+                worst = std::max(worst, worst_rel_gnorm(ctxs[i]));
+            }
+            converged = worst <= rel_tol;
+        }
+    }
+    if (iters_done) *iters_done = done;
+    if (last) {
+        for (int32_t i = 0; i < n; ++i) {
+            if ((s = read_scalars(ctxs[i])) != ALS_OK) return s;
+            fill_info(ctxs[i], last + i);
+            last[i].kernels = nk[i];
+        }
+    }
+    return ALS_OK;
+}

@@ -247,6 +247,17 @@ def make_batch(n_prob, nnz_lo, nnz_hi, dens_lo, dens_hi, seed, rank=10):
     return probs
 
 
+C4_NF = (10, 20, 50, 100)
+
+
+def c4_problems(n_prob=64, nnz_lo=10_000, nnz_hi=10_000_000, seed=4):
+    """The batched-uneven workload: n_prob independent problems, ratings
+    log-uniform in [nnz_lo, nnz_hi], density in 0.1-5%, n_f assigned round
+    robin over C4_NF.  Returns (problems, n_fs)."""
+    probs = make_batch(n_prob, nnz_lo, nnz_hi, 0.001, 0.05, seed)
+    return probs, [C4_NF[q % len(C4_NF)] for q in range(n_prob)]
+
+
 def init_factors(n_u, n_m, n_f, seed):
     """x_0 (Eq. 5 layout, n_u rows then n_m rows of n_f): i.i.d. N(0, 1/n_f)."""
     rng = np.random.Generator(np.random.PCG64(seed))
