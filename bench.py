@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving", "batched"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving", "batched", "scale"])
+    ap.add_argument("--scale-steps", default="1e7,3e7,1e8,3e8,1e9", help="scale: ratings steps")
+    ap.add_argument("--scale-nf", default="10,50", help="scale: n_f values")
     ap.add_argument("--n-prob", type=int, default=64, help="batched: number of problems")
     ap.add_argument("--rates", default="1e3,1e4,1e5", help="serving: Poisson arrival rates (req/s)")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals per rate")
@@ -268,6 +270,65 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def run_scale(args):
+    """Scaling sweep: Zipf(1.1) ratings from 1e7 to 1e9 (generated on the GPU),
+    n_f in {10, 50}, mixed precision, FP32 factors: per step the context build
+    (ratings builder) time, the autotuner's choice, 10 timed ALS-NCG iterations
+    and one timed sweep, as ratings x iterations / s and ratings / s per
+    sweep."""
+    import torch
+    import synth
+    from paper_1508_03110_gb300 import ALS
+
+    results = []
+    for step in args.scale_steps.split(","):
+        n_u, n_m, target = synth.SCALE_STEPS[step]
+        t0 = time.perf_counter()
+        rows, cols, vals = synth.make_scale_gpu(n_u, n_m, target, seed=40)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        nnz = int(rows.shape[0])
+        for nf in (int(x) for x in args.scale_nf.split(",")):
+            stream = torch.cuda.Stream()
+            torch.cuda.reset_peak_memory_stats()
+            t0 = time.perf_counter()
+            m = ALS(n_u, n_m, rows, cols, vals, nf, 0.05, precision="mixed", stream=stream)
+            m.sync()
+            build_s = time.perf_counter() - t0
+            x0 = torch.randn((n_u + n_m) * nf, generator=torch.Generator("cuda").manual_seed(41), device="cuda",
+                             dtype=torch.float32) / float(np.sqrt(nf))
+            m.set_factors(x0[: n_u * nf].view(n_u, nf), x0[n_u * nf:].view(n_m, nf))
+            tune = m.autotune(reps=1)
+            m.run(2, 0.0, check_every=2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = m.run(10, 0.0, check_every=10)
+            e1.record(stream)
+            e1.synchronize()
+            t_it = e0.elapsed_time(e1) / 1e3 / 10
+            e0.record(stream)
+            m.sweep(1)
+            e1.record(stream)
+            e1.synchronize()
+            t_sw = e0.elapsed_time(e1) / 1e3
+            res = {"step": step, "n_u": n_u, "n_m": n_m, "ratings": nnz, "target": target, "n_f": nf,
+                   "generate_s": gen_s, "build_s": build_s, "ms_per_iter": t_it * 1e3,
+                   "ratings_iter_per_s": nnz / t_it, "sweep_ms": t_sw * 1e3, "ratings_per_s_per_sweep": nnz / t_sw,
+                   "gnorm_rel_after_12": info["gnorm"] / info["gnorm0"],
+                   "peak_torch_gb": torch.cuda.max_memory_allocated() / 1e9,
+                   "launch": {k: tune[k] for k in ("heavy_min", "grid_mult", "split_min", "seg_len", "gram_path",
+                                                   "sweep_bin_min")}}
+            results.append(res)
+            print(json.dumps(res), file=sys.stderr, flush=True)
+            m.close()
+            del x0
+        del rows, cols, vals
+        torch.cuda.empty_cache()
+    print(json.dumps({"mode": "scale", "workload": "Zipf(1.1) users and items, rank-10 half-star values, "
+                      "lambda 0.05, mixed precision, FP32 factors, int32 indices", "results": results}), flush=True)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -418,6 +479,9 @@ def main():
         return
     if args.mode == "batched":
         run_batched(args)
+        return
+    if args.mode == "scale":
+        run_scale(args)
         return
     import torch
     import synth

@@ -334,7 +334,9 @@ ALS_API void als_server_destroy(als_server *srv);
  *   split_min      rows with at least this many ratings are split into
  *                  segments of about seg_len ratings whose partial Gram
  *                  matrices and right-hand sides / residuals are formed by
- *                  separate CTAs and added in FP64 (0 = no splitting)
+ *                  separate CTAs and added in FP64 (0 = no splitting; in the
+ *                  mixed form rows of more than ~1e5 ratings need splitting
+ *                  for accuracy, and the autotuner never goes above 65536)
  *   gram_path      ALS_GRAM_FMA or ALS_GRAM_TC (the latter ALS_MIXED only)
  * ------------------------------------------------------------------------- */
 typedef struct {

@@ -1108,8 +1108,12 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
         if ((s = trial(cand, false, best)) != ALS_OK) return s;
     }
     {
-        const int split_c[][2] = {{0, 2048}, {2048, 1024}, {2048, 2048}, {4096, 1024}, {4096, 2048},
-                                  {4096, 4096}, {8192, 2048}, {8192, 4096}, {16384, 4096}};
+        // every candidate splits rows above 65536 ratings: a whole row's
+        // Gram matrix accumulated in FP32 over millions of ratings is too
+        // inexact for the mixed form's refinement (f 1.4e-5 off the FP64 run
+        // with rows of 2.7e6 ratings); segment partials added in FP64 are not
+        const int split_c[][2] = {{2048, 1024}, {2048, 2048}, {4096, 1024}, {4096, 2048}, {4096, 4096},
+                                  {8192, 2048}, {8192, 4096}, {16384, 4096}, {65536, 4096}};
         for (const auto &sc : split_c) {
             als_launch cand = cur;
             cand.split_min = sc[0];

@@ -6,3 +6,4 @@ from .ratings import (  # noqa: F401
     Ratings, CONFIGS, make_config, make_ratings, init_factors, rank_degrees,
     sample_distinct, half_star_values, make_dense, foldin_requests, make_batch, c4_problems, C4_NF,
 )
+from .scale_gpu import SCALE_STEPS, make_scale_gpu  # noqa: F401,E402
