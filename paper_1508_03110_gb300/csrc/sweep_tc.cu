@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             }
             __syncthreads();
             // ---- 4. Cholesky (inverted diagonal blocks), refinement ------------
-            ok = chol_blocked128(A, ldA, nf, diag, work, t);
+            ok = chol_blocked128(A, ldA, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
             if (ok) invert_diag_blocks128(A, ldA, nf, diag, t);
             if (!ok && t == 0) atomicAdd(a.notspd, 1);
         }
