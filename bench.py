@@ -75,7 +75,8 @@ TOLS = (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
 def run_s_to_tol(args):
     """Seconds to reach |g_k| / |g_0| <= tol from the same x_0: mixed ALS-NCG,
     FP64 ALS-NCG and plain FP64 ALS (Algorithm 1; as in the paper, the time
-    spent evaluating |g| for ALS is excluded).  Each method stops at the
+    spent evaluating |g| for ALS is excluded).  Each context is autotuned
+    once before its clock starts.  Each method stops at the
     tolerance or after `budget` seconds of its own iterations."""
     import torch
     import synth
@@ -90,6 +91,7 @@ def run_s_to_tol(args):
     def ncg(prec):
         m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision=prec, stream=stream)
         m.set_x(x0)
+        m.autotune(reps=1)  # setup, like the ratings builder: not timed
         traj, elapsed, k = [], 0.0, 0
         step = 10 if prec == "mixed" else 2
         while elapsed < args.budget:
@@ -108,6 +110,7 @@ def run_s_to_tol(args):
     def als64():
         m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision="fp64", stream=stream)
         m.set_x(x0)
+        m.autotune(reps=1)
         _, g0 = m.grad(want_vector=False)
         traj, elapsed, k = [], 0.0, 0
         while elapsed < args.budget:
@@ -515,6 +518,12 @@ def main():
         tune = m.autotune(reps=2)
     launch = m.get_launch()
     m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
+    # DRAM bytes (read + write) of one sweep's two k_sweep_tc launches, from an
+    # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command
+    # on this workload with the shapes the autotuner picks for it (no split
+    # rows); other workloads have no capture
+    traffic = 7.94e8 if (args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
+                         and launch["split_min"] > 33108) else None
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
     sampler = ClockSampler(local)
@@ -573,7 +582,7 @@ def main():
         unit, bound = "TFLOP/s", "alu"
         achieved = fl / t_sweep / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per sweep (U + M launch), ncu",
                 "kernel": "k_sweep_tc (fused gather, tensor-core Gram, Cholesky, solves)" if use_tc
                 else "k_sweep_fma (fused Gram, Cholesky, solves)",
                 "peak_source": peak_note, "sweep_ms": t_sweep * 1e3,
