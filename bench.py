@@ -458,6 +458,22 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(t, dist):
+    """The slowest replica's time: the job is done when every rank is."""
+    if dist is None:
+        return t
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, t):
+    """Whole-job rate: every rank processed units_per_rank in at most t."""
+    return units_per_rank * world / t
+
+
 def workload_name(args, r):
     return (f"{args.workload}: synthetic {r.n_u:,} users x {r.n_m:,} items, {r.nnz:,} ratings, "
             f"n_f={r.n_f}, lambda={r.lam}")
@@ -540,11 +556,8 @@ def main():
     t = e0.elapsed_time(e1) / 1e3
     barrier()
     clocks = sampler.stop()
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = r.nnz * args.steps * world / t
+    t = max_over_ranks(t, dist)
+    value = job_throughput(r.nnz * args.steps, world, t)
     launches = int(info["kernels"])
 
     # ---- the dominant kernel: the fused sweep (U half + M half launches) ----
@@ -617,13 +630,10 @@ def main():
         U, M = me.get_factors()
         te = time.perf_counter() - t0
         me.close()
-        if dist is not None:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, dist)
         h2d = r.nnz * 12 + x0.nbytes
         d2h = U.nbytes + M.nbytes
-        e2e = {"value": r.nnz * args.steps * world / te, "unit": UNIT,
+        e2e = {"value": job_throughput(r.nnz * args.steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context build from host COO, x0 upload, K iterations, factor download"}
 
