@@ -381,6 +381,18 @@ ALS_API als_status als_autotune(als_ctx *ctx, int32_t reps, als_tune_report *out
 ALS_API als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter, double rel_tol,
                                  int32_t check_every, als_iter_info *last, int32_t *iters_done);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  Runs
+ * one user half sweep of the tensor-core kernel in which no MMA is issued and
+ * nothing signals its mbarriers, so every CTA's bounded wait runs out after
+ * limit_s (0 < limit_s <= 10): each CTA records the expiry, frees its TMEM
+ * and returns, with nothing left in flight.  Returns ALS_ETIMEOUT when the
+ * waits ran out as designed (*expired = CTAs that gave up, one per user row
+ * with ratings); the context stays usable: its flags are cleared and its
+ * factors and NCG state are untouched (only scratch is written).
+ * ALS_ENOTSUP unless the context uses the tensor-core Gram.  Note that
+ * n_u x limit_s / (4 x SMs) seconds pass: use a small problem. */
+ALS_API als_status als_selftest_wait_expiry(als_ctx *ctx, double limit_s, int64_t *expired);
+
 /* Wait for all work enqueued by this context. */
 ALS_API als_status als_sync(als_ctx *ctx);
 

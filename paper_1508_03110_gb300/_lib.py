@@ -102,6 +102,7 @@ SIGNATURES = {
     "als_autotune": (_i32, [_vp, _i32, ctypes.POINTER(TuneReport)]),
     "als_group_run": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _dbl, _i32, ctypes.POINTER(IterInfo),
                              ctypes.POINTER(_i32)]),
+    "als_selftest_wait_expiry": (_i32, [_vp, _dbl, ctypes.POINTER(_i64)]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
     "als_last_error": (ctypes.c_char_p, []),

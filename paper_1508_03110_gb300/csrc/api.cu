@@ -1192,3 +1192,54 @@ extern "C" als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter,
     }
     return ALS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device waits: one half sweep of the tensor-core
+// kernel in which no MMA is issued and nothing signals the mbarriers, so every
+// CTA's wait runs out after limit_s; each records the expiry, frees its TMEM
+// and returns.  Nothing is left in flight; the flags are cleared afterwards.
+
+extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64_t *expired) {
+    if (!c || !(limit_s > 0.0) || limit_s > 10.0) {
+        als_set_error("als_selftest_wait_expiry: bad argument (0 < limit_s <= 10)");
+        return ALS_EINVAL;
+    }
+    if (!c->use_tc) {
+        als_set_error("als_selftest_wait_expiry: needs the tensor-core Gram (ALS_MIXED)");
+        return ALS_ENOTSUP;
+    }
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream));
+    SweepArgs a;
+    a.ptr = c->uptr;
+    a.idx = c->uidx;
+    a.val = c->uval;
+    a.order = c->uorder;
+    a.nrows = c->n_u;
+    a.F = mblk(c, c->X);
+    a.Xin = ublk(c, c->X);
+    a.Xout = c->tmpvec;   // scratch: the factors are not touched
+    a.Gbar = nullptr;
+    a.nf = c->nf;
+    a.ld = c->ld;
+    a.lambda = c->cfg.lambda;
+    a.refine = c->cfg.refine_steps;
+    a.notspd = c->dflags;
+    a.timeout = c->dflags + 7;
+    a.wait_ns = (uint64_t)(limit_s * 1e9);
+    a.withhold = 1;
+    als_status s = launch_sweep(c, a, false, true);
+    if (s != ALS_OK) return s;
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int64_t n = c->hflags[7];
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream));
+    ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (expired) *expired = n;
+    if (n == 0) {
+        als_set_error("als_selftest_wait_expiry: no wait ran out");
+        return ALS_OK;
+    }
+    als_set_error("als_selftest_wait_expiry: the bounded waits ran out as designed");
+    return ALS_ETIMEOUT;
+}

@@ -185,6 +185,8 @@ struct SweepArgs {
     int *timeout;           // set when a bounded device wait expired
     cudaStream_t stream = nullptr;  // launch stream (nullptr: the context's)
     int64_t nbig = 0;       // FMA sweep: the first nbig rows of `order` get a CTA each
+    uint64_t wait_ns = 2000000000ull;  // limit of each bounded device wait
+    int withhold = 0;       // self-test of the waits: no MMA is issued, so every wait runs out
     // segment mode (split heavy rows): "row" r is segment r, a slice
     // [seg_beg[r], seg_beg[r] + seg_len[r]) of the ratings of row
     // order[seg_row[r]]; the kernel writes that slice's partial Gram matrix

@@ -38,7 +38,6 @@ constexpr int STAGE_BYTES = 2 * TILE_BYTES;      // H and L
 constexpr int NSTAGE = 2;
 constexpr uint32_t LBO = 1024;  // byte distance between the two 64-wide MN atoms
 constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
-constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int TMEM_COLS = 128;
 
 struct TcLayout {
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             for (int ch = 0; ch < nch; ++ch) {
                 const int st = ch & 1;
                 if (pend[st]) {  // the MMAs of chunk ch-2 still read stage st
-                    const bool w = mbar_wait_bounded(mbar[st], phase[st], WAIT_NS);
+                    const bool w = mbar_wait_bounded(mbar[st], phase[st], a.wait_ns);
                     if (__syncthreads_or(!w)) { bail = true; break; }
                     phase[st] ^= 1u;
                     pend[st] = 0;
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                 }
                 fence_proxy_async_smem();
                 __syncthreads();
-                if (t == 0) {
+                if (t == 0 && !a.withhold) {
                     tc_fence_after();
                     const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
 #pragma unroll
@@ -216,7 +215,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
             if (bail) break;
             for (int s = 0; s < 2; ++s) {
                 if (pend[s]) {
-                    const bool w = mbar_wait_bounded(mbar[s], phase[s], WAIT_NS);
+                    const bool w = mbar_wait_bounded(mbar[s], phase[s], a.wait_ns);
                     if (__syncthreads_or(!w)) { bail = true; break; }
                     phase[s] ^= 1u;
                     pend[s] = 0;
