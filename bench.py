@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--jobs", type=int, default=2, help="serving: factorisation jobs per rate")
     ap.add_argument("--tol", type=float, default=1e-6, help="s_to_tol: relative |g| tolerance")
     ap.add_argument("--budget", type=float, default=300.0, help="s_to_tol: seconds per method")
+    ap.add_argument("--methods", default="mixed_alsncg,fp64_alsncg,fp64_als", help="s_to_tol: methods to run")
     return ap.parse_args()
 
 
@@ -129,6 +130,8 @@ def run_s_to_tol(args):
 
     for name, fn in (("mixed_alsncg", lambda: ncg("mixed")), ("fp64_alsncg", lambda: ncg("fp64")),
                      ("fp64_als", als64)):
+        if name not in args.methods.split(","):
+            continue
         traj = fn()
         first = {}
         for tol in TOLS:

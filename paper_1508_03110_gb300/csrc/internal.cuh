@@ -110,7 +110,7 @@ struct als_ctx {
     int32_t *hseg_off[2] = {nullptr, nullptr};   // [nsplit + 1] first segment of each split row
     void *seg_part = nullptr;          // partials: max nseg x seg_stride (element size esz)
     int64_t seg_stride = 0;
-    float *hfac = nullptr;             // mixed: factored matrices of the split rows, n_f x (n_f + 1) each
+    float *hfac = nullptr;             // mixed: factored matrices of the split rows, packed lower triangles
     int32_t *hflag = nullptr;          // mixed: split rows that take another correction
 
     // batched problems (n_prob > 1): block-diagonal layout, per-problem scalars

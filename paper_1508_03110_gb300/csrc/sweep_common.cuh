@@ -170,6 +170,10 @@ __device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int
     return d2 * rho * rho <= T(0x1p-42) * u2;
 }
 
+// Packed lower-triangular storage of the symmetric matrices of the
+// tensor-core path: entry (i, j), j <= i, at tri_off(i) + j.
+__device__ __forceinline__ int tri_off(int i) { return i * (i + 1) / 2; }
+
 // ---------------------------------------------------------------------------
 // Blocked right-looking Cholesky (panels of 8 columns) for n <= 128, FP32, by
 // a CTA of exactly 128 threads, two CTA barriers per panel:
@@ -189,7 +193,7 @@ __device__ __forceinline__ bool sw_correction_small(const T *dx, const T *u, int
 // A: lower triangle used; on return its lower triangle holds L (diagonal
 // included) and diag[k] = 1 / L[k][k].  work: >= 8*128 + 64 + 1 floats,
 // 16-byte aligned.  Returns false (in every thread) on a non-positive pivot.
-__device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float *diag, float *work, int t,
+__device__ __forceinline__ bool chol_blocked128(float *A, int n, float *diag, float *work, int t,
                                                 int lead = 0) {
     float *PT = work;              // [8][128] L21, transposed
     float *Lk = work + 8 * 128;    // [8][8] L_kk, Lk[c * 8 + r] = L[r][c]
@@ -203,7 +207,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j <= i; ++j)
-                    d[i * (i + 1) / 2 + j] = (i < nb && j < nb) ? A[(kb + i) * ldA + kb + j] : (i == j ? 1.0f : 0.0f);
+                    d[i * (i + 1) / 2 + j] = (i < nb && j < nb) ? A[tri_off(kb + i) + kb + j] : (i == j ? 1.0f : 0.0f);
             bool bad = false;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -226,7 +230,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
 #pragma unroll
                 for (int j = 0; j <= i; ++j) {
                     Lk[j * 8 + i] = d[i * (i + 1) / 2 + j];
-                    if (i < nb && j < nb) A[(kb + i) * ldA + kb + j] = d[i * (i + 1) / 2 + j];
+                    if (i < nb && j < nb) A[tri_off(kb + i) + kb + j] = d[i * (i + 1) / 2 + j];
                 }
         }
         __syncthreads();
@@ -237,7 +241,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
         const bool own = t >= nb && t < mp;
         if (own) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) a[c] = (c < nb) ? A[(kb + t) * ldA + kb + c] : 0.0f;
+            for (int c = 0; c < 8; ++c) a[c] = (c < nb) ? A[tri_off(kb + t) + kb + c] : 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 a[c] *= diag[kb + c];
@@ -246,7 +250,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                if (c < nb) A[(kb + t) * ldA + kb + c] = a[c];
+                if (c < nb) A[tri_off(kb + t) + kb + c] = a[c];
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) PT[c * 128 + t] = own ? a[c] : 0.0f;
@@ -278,7 +282,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
                         acc[4 * v + 3] = fmaf(li, w.w, acc[4 * v + 3]);
                     }
                 }
-                float *ar = A + (kb + i) * ldA + kb + j0;
+                float *ar = A + tri_off(kb + i) + kb + j0;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if (j0 + k <= i) ar[k] -= acc[k];
@@ -294,7 +298,7 @@ __device__ __forceinline__ bool chol_blocked128(float *A, int ldA, int n, float 
 // by 16 threads, then the rows outside the block are updated by all 128
 // threads.  Every dot product is a fixed 16-term loop (predicated), so its
 // shared-memory loads issue together.  b is consumed; z scratch; x result.
-__device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, float *b, float *z, float *x,
+__device__ __forceinline__ void trisolve_inv128(const float *A, int n, float *b, float *z, float *x,
                                                 int t) {
     for (int kb = 0; kb < n; kb += 16) {
         const int nb = min(16, n - kb);
@@ -303,8 +307,8 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
             float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                if (c <= t) s0 = fmaf(A[(kb + t) * ldA + kb + c], b[kb + c], s0);
-                if (c + 1 <= t) s1 = fmaf(A[(kb + t) * ldA + kb + c + 1], b[kb + c + 1], s1);
+                if (c <= t) s0 = fmaf(A[tri_off(kb + t) + kb + c], b[kb + c], s0);
+                if (c + 1 <= t) s1 = fmaf(A[tri_off(kb + t) + kb + c + 1], b[kb + c + 1], s1);
             }
             z[kb + t] = s0 + s1;
         }
@@ -313,8 +317,8 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
             float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                if (c < nb) s0 = fmaf(A[i * ldA + kb + c], z[kb + c], s0);
-                if (c + 1 < nb) s1 = fmaf(A[i * ldA + kb + c + 1], z[kb + c + 1], s1);
+                if (c < nb) s0 = fmaf(A[tri_off(i) + kb + c], z[kb + c], s0);
+                if (c + 1 < nb) s1 = fmaf(A[tri_off(i) + kb + c + 1], z[kb + c + 1], s1);
             }
             b[i] -= s0 + s1;
         }
@@ -327,8 +331,8 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
             float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                if (c >= t && c < nb) s0 = fmaf(A[(kb + c) * ldA + kb + t], z[kb + c], s0);
-                if (c + 1 >= t && c + 1 < nb) s1 = fmaf(A[(kb + c + 1) * ldA + kb + t], z[kb + c + 1], s1);
+                if (c >= t && c < nb) s0 = fmaf(A[tri_off(kb + c) + kb + t], z[kb + c], s0);
+                if (c + 1 >= t && c + 1 < nb) s1 = fmaf(A[tri_off(kb + c + 1) + kb + t], z[kb + c + 1], s1);
             }
             x[kb + t] = s0 + s1;
         }
@@ -337,8 +341,8 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
             float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                if (c < nb) s0 = fmaf(A[(kb + c) * ldA + i], x[kb + c], s0);
-                if (c + 1 < nb) s1 = fmaf(A[(kb + c + 1) * ldA + i], x[kb + c + 1], s1);
+                if (c < nb) s0 = fmaf(A[tri_off(kb + c) + i], x[kb + c], s0);
+                if (c + 1 < nb) s1 = fmaf(A[tri_off(kb + c + 1) + i], x[kb + c + 1], s1);
             }
             z[i] -= s0 + s1;
         }
@@ -351,7 +355,7 @@ __device__ __forceinline__ void trisolve_inv128(const float *A, int ldA, int n, 
 // t % 16 of block t / 16 by forward substitution (n <= 128: 8 blocks x 16
 // columns = 128 threads).  diag holds 1 / L[k][k].  Afterwards the solves of
 // trisolve_inv128 apply.
-__device__ __forceinline__ void invert_diag_blocks128(float *A, int ldA, int n, const float *diag, int t) {
+__device__ __forceinline__ void invert_diag_blocks128(float *A, int n, const float *diag, int t) {
     const int b = t >> 4, j = t & 15, kb = 16 * b;
     const int nb = kb < n ? min(16, n - kb) : 0;
     float inv[16];
@@ -365,7 +369,7 @@ __device__ __forceinline__ void invert_diag_blocks128(float *A, int ldA, int n, 
                 float s = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (c >= j && c < i) s = fmaf(A[(kb + i) * ldA + kb + c], inv[c], s);
+                    if (c >= j && c < i) s = fmaf(A[tri_off(kb + i) + kb + c], inv[c], s);
                 v = -s * diag[kb + i];
             }
         }
@@ -375,7 +379,7 @@ __device__ __forceinline__ void invert_diag_blocks128(float *A, int ldA, int n, 
     if (j < nb) {
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-            if (i < nb && i >= j) A[(kb + i) * ldA + kb + j] = inv[i];
+            if (i < nb && i >= j) A[tri_off(kb + i) + kb + j] = inv[i];
     }
     __syncthreads();
 }

@@ -11,7 +11,8 @@
 //   2. one CTA per split row adds its segments' partials in FP64 in segment
 //      order (deterministic), adds lambda n_i I, factors and solves -- the
 //      FP64 form exactly (the definition), the mixed form as the first
-//      correction of the refinement from x_i -- and keeps the factored matrix;
+//      correction of the refinement from x_i -- and keeps the factored matrix
+//      (mixed form: packed lower triangle, as the tensor-core kernel's);
 //   3. mixed form only, up to refine_steps - 1 times, for the rows whose last
 //      correction was not yet negligible: one CTA per segment forms its part
 //      of the FP32 residual at the new row, one CTA per row adds them, solves
@@ -78,20 +79,25 @@ __global__ void __launch_bounds__(HT) k_split_solve(SplitArgs s) {
     const T *P = reinterpret_cast<const T *>(s.part);
     const T *xi = s.Xin ? reinterpret_cast<const T *>(s.Xin) + row * s.ld : nullptr;
     for (int k = t; k < nf; k += HT) u[k] = xi ? xi[k] : T(0);
+    // FP64 form: square A (column Cholesky); mixed form: packed lower triangle
     for (int e = t; e < tri + nf; e += HT) {
         double acc = 0.0;
         for (int q = s0; q < s1; ++q) acc += (double)P[(int64_t)q * s.seg_stride + e];
         if (e < tri) {
-            int m, c;
-            tri_index(e, m, c);
-            A[m * ldA + c] = (T)acc;
+            if constexpr (sizeof(T) == 8) {
+                int m, c;
+                tri_index(e, m, c);
+                A[m * ldA + c] = (T)acc;
+            } else {
+                A[e] = (T)acc;
+            }
         } else {
             v1[e - tri] = (T)acc;
         }
     }
     __syncthreads();
     if (t < nf) {
-        A[t * ldA + t] += lam_n;
+        A[sizeof(T) == 8 ? t * ldA + t : tri_off(t) + t] += lam_n;
         if (sizeof(T) == 4) v1[t] -= lam_n * u[t];  // mixed: residual at x_i
     }
     __syncthreads();
@@ -100,13 +106,14 @@ __global__ void __launch_bounds__(HT) k_split_solve(SplitArgs s) {
         ok = sw_cholesky<T, HT>(A, ldA, nf, colk, diag, t);
         if (ok) sw_trisolve<T, HT>(A, ldA, nf, diag, v1, v2, u, t);
     } else {
-        ok = chol_blocked128(A, ldA, nf, diag, work, t);
+        ok = chol_blocked128(reinterpret_cast<float *>(A), nf, reinterpret_cast<float *>(diag), work, t);
         if (ok) {
-            invert_diag_blocks128(A, ldA, nf, diag, t);
-            trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
+            invert_diag_blocks128(reinterpret_cast<float *>(A), nf, reinterpret_cast<float *>(diag), t);
+            trisolve_inv128(reinterpret_cast<float *>(A), nf, reinterpret_cast<float *>(v1),
+                            reinterpret_cast<float *>(v2), reinterpret_cast<float *>(colk), t);
             for (int k = t; k < nf; k += HT) u[k] += colk[k];
-            float *hf = s.hfac + (size_t)h * nf * ldA;
-            for (int e = t; e < nf * ldA; e += HT) hf[e] = A[e];
+            float *hf = s.hfac + (size_t)h * tri;
+            for (int e = t; e < tri; e += HT) hf[e] = A[e];
             __syncthreads();
             const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)n, work, t);
             if (t == 0) s.hflag[h] = (s.more > 0 && !small) ? 1 : 0;
@@ -168,15 +175,16 @@ __global__ void __launch_bounds__(HT) k_split_refine(SplitArgs s) {
     const int s0 = s.hseg_off[h], s1 = s.hseg_off[h + 1];
     const float *P = reinterpret_cast<const float *>(s.part);
     float *xo = reinterpret_cast<float *>(s.Xout) + row * s.ld;
-    const float *hf = s.hfac + (size_t)h * nf * ldA;
-    for (int e = t; e < nf * ldA; e += HT) A[e] = hf[e];
+    const int tri0 = nf * (nf + 1) / 2;
+    const float *hf = s.hfac + (size_t)h * tri0;
+    for (int e = t; e < tri0; e += HT) A[e] = hf[e];
     for (int k = t; k < nf; k += HT) {
         double acc = 0.0;
         for (int q = s0; q < s1; ++q) acc += (double)P[(int64_t)q * s.seg_stride + tri + k];
         u[k] = xo[k];
         v1[k] = (float)acc - lam_n * u[k];
     }
-    trisolve_inv128(A, ldA, nf, v1, v2, colk, t);  // starts with a barrier
+    trisolve_inv128(A, nf, v1, v2, colk, t);  // starts with a barrier
     for (int k = t; k < nf; k += HT) u[k] += colk[k];
     __syncthreads();
     const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)n, red, t);
@@ -286,7 +294,8 @@ als_status build_split(als_ctx *c) {
     if ((st = ctx_alloc(c, &p, (size_t)max_seg * c->seg_stride * c->esz)) != ALS_OK) return st;
     c->seg_part = p;
     if (!c->f64) {
-        if ((st = ctx_alloc(c, &p, (size_t)max_split * c->nf * (c->nf + 1) * sizeof(float))) != ALS_OK) return st;
+        if ((st = ctx_alloc(c, &p, (size_t)max_split * (c->nf * (c->nf + 1) / 2) * sizeof(float))) != ALS_OK)
+            return st;
         c->hfac = (float *)p;
         if ((st = ctx_alloc(c, &p, (size_t)max_split * sizeof(int32_t))) != ALS_OK) return st;
         c->hflag = (int32_t *)p;

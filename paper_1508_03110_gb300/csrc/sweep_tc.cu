@@ -49,23 +49,23 @@ __host__ __device__ inline TcLayout tc_layout(int nf) {
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
     int big = NSTAGE * STAGE_BYTES;
-    const int a_bytes = nf * (nf + 1) * 4;
+    const int a_bytes = nf * (nf + 1) / 2 * 4;  // packed lower triangle
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
     L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
-    L.mbar = L.vec + (5 * 128 + 16 * 128 + 256 + 16) * 4;
+    L.mbar = L.vec + (5 * 128 + 1104) * 4;
     L.holder = L.mbar + 16;
     L.total = L.holder + 16;
     return L;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc) {
+__global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char *base = smem_raw + pad;
     const uint32_t sbase = raw + pad;
-    const int nf = a.nf, ldA = nf + 1;
+    const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const TcLayout L = tc_layout(nf);
     float *A = reinterpret_cast<float *>(base + L.A);
@@ -81,17 +81,15 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
         mbar_init(mbar[1], 1);
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(sbase + L.holder, TMEM_COLS);
-    tc_fence_before();
     __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *holder;
+    uint32_t tmem = 0;
+    bool held = false;  // TMEM columns are held only from a row's Gram to its read-out
     const uint32_t idesc = idesc_bf16_f32_mn((uint32_t)ntc);
     const float *F = reinterpret_cast<const float *>(a.F);
     uint32_t phase[2] = {0u, 0u};
     bool bail = false;
 
-    for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+    for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {  // one row per CTA (grid = rows)
         const bool seg = a.seg_out != nullptr;  // a slice of a split row: partials only
         const int64_t row = seg ? a.order[a.seg_row[r]] : (a.order ? a.order[r] : r);
         const int64_t beg = seg ? a.seg_beg[r] : a.ptr[row];
@@ -108,6 +106,15 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
         for (int i = 0; i < 4; ++i) uu[i] = (xi && 4 * lane + i < nf) ? xi[4 * lane + i] : 0.0f;
         for (int k = t; k < nf; k += TC_THREADS) u[k] = xi ? xi[k] : 0.0f;
         if (ok) {
+            // TMEM for this row's accumulator (5 CTAs share an SM's 512 columns:
+            // if none are free the allocation waits for a CTA that is past its
+            // read-out, which every CTA reaches after bounded waits)
+            if (warp == 0) tmem_alloc(sbase + L.holder, TMEM_COLS);
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            tmem = *holder;
+            held = true;
             // ---- 1-2. gather + tensor-core Gram, with the first FP32 residual
             //      r0 = sum_e f_e (r_e - f_e . u0) of the chunk's ratings computed
             //      while the chunk's copies and MMAs are in flight -------------
@@ -185,9 +192,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                             for (int i = 0; i < 2; ++i) {
                                 const __nv_bfloat16 h0 = __float2bfloat16_rn(f[q][2 * i]);
                                 const __nv_bfloat16 h1 = __float2bfloat16_rn(f[q][2 * i + 1]);
-                                const __nv_bfloat16 l0 = __float2bfloat16_rn(2.0f * (f[q][2 * i] - __bfloat162float(h0)));
-                                const __nv_bfloat16 l1 =
-                                    __float2bfloat16_rn(2.0f * (f[q][2 * i + 1] - __bfloat162float(h1)));
+                                const __nv_bfloat16 l0 = __float2bfloat16_rn(f[q][2 * i] - __bfloat162float(h0));
+                                const __nv_bfloat16 l1 = __float2bfloat16_rn(f[q][2 * i + 1] - __bfloat162float(h1));
                                 hw[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
                                 lw[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                             }
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                         const uint64_t dl = smem_desc_sw128(stage + TILE_BYTES + (uint32_t)s * 2u * SBO, LBO, SBO);
                         tc_mma_bf16(tmem, dh, dh, idesc, (ch > 0 || s > 0) ? 1u : 0u);
                         tc_mma_bf16(tmem, dh, dl, idesc, 1u);
+                        tc_mma_bf16(tmem, dl, dh, idesc, 1u);
                     }
                     tc_commit(mbar[st]);
                 }
@@ -235,44 +242,39 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int col = c0 + i;
-                            if (col < nf) A[m * ldA + col] = v[i];
+                            if (col <= m) A[tri_off(m) + col] = v[i];
                         }
                     }
                 }
             }
             tc_fence_before();
             __syncthreads();
+            if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);  // read out: another CTA may take it
+            held = false;
             if (seg) {
-                // the slice's partials: packed lower triangle of the symmetric
-                // part of D (row m at m (m + 1) / 2), then its residual at u0
+                // the slice's partials: D's lower triangle, packed as A is
+                // (row m at m (m + 1) / 2), then its residual at u0
                 float *po = reinterpret_cast<float *>(a.seg_out) + r * a.seg_stride;
                 const int tri = nf * (nf + 1) / 2;
-                for (int e = t; e < tri; e += TC_THREADS) {
-                    int m = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-                    while ((m + 1) * (m + 2) / 2 <= e) ++m;
-                    while (m * (m + 1) / 2 > e) --m;
-                    const int cc = e - m * (m + 1) / 2;
-                    po[e] = 0.5f * (A[m * ldA + cc] + A[cc * ldA + m]);
-                }
+                for (int e = t; e < tri; e += TC_THREADS) po[e] = A[e];
                 if (t < nf) po[tri + t] = (part[t] + part[128 + t]) + (part[256 + t] + part[384 + t]);
                 __syncthreads();
                 continue;
             }
-            // symmetric part of D, lower triangle, plus lambda n I; the first
-            // residual v1 = r0 - lambda n u0 (fixed order over the warps)
+            // A = D + lambda n I (lower triangle); the first residual
+            // v1 = r0 - lambda n u0 (fixed order over the warps)
             if (t < nf) {
-                for (int c = 0; c < t; ++c) A[t * ldA + c] = 0.5f * (A[t * ldA + c] + A[c * ldA + t]);
-                A[t * ldA + t] += lam_n;
+                A[tri_off(t) + t] += lam_n;
                 v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
             }
             __syncthreads();
             // ---- 4. Cholesky (inverted diagonal blocks), refinement ------------
-            ok = chol_blocked128(A, ldA, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
-            if (ok) invert_diag_blocks128(A, ldA, nf, diag, t);
+            ok = chol_blocked128(A, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
+            if (ok) invert_diag_blocks128(A, nf, diag, t);
             if (!ok && t == 0) atomicAdd(a.notspd, 1);
         }
         if (ok) {
-            trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
+            trisolve_inv128(A, nf, v1, v2, colk, t);
             for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             for (int s = 1; s < a.refine; ++s) {
                 if (sw_correction_small<float, TC_THREADS>(colk, u, nf, n, part, t)) break;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
                 for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = ak[i] - ck[i];
                 __syncthreads();
                 if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
-                trisolve_inv128(A, ldA, nf, v1, v2, colk, t);
+                trisolve_inv128(A, nf, v1, v2, colk, t);
                 for (int k = t; k < nf; k += TC_THREADS) u[k] += colk[k];
             }
         } else {
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_sweep_tc(SweepArgs a, int ntc
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (held && warp == 0) tmem_dealloc(tmem, TMEM_COLS);
     if (bail && t == 0) atomicAdd(a.timeout, 1);
 }
 
@@ -318,19 +320,22 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
     }
     const int ntc = (a.nf + 15) / 16 * 16;
     const TcLayout L = tc_layout(a.nf);
-    // 46..56 KB of shared memory per CTA keeps exactly 4 CTAs (4 x 128 TMEM
-    // columns = the SM's 512) resident per SM, so tcgen05.alloc never waits.
+    // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM
     size_t smem = (size_t)L.total + 1024;
-    if (smem < 46 * 1024) smem = 46 * 1024;
     if (raise_smem_limit((const void *)k_sweep_tc, smem) != ALS_OK) return ALS_ECUDA;
-    // the whole L1/shared array as shared memory, so that 4 CTAs fit per SM
+    // the whole L1/shared array as shared memory, so that 5 CTAs fit per SM
     ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     // One CTA per row (rows in degree-descending order): the hardware keeps as
-    // many CTAs resident per SM as shared memory allows (at most 4 here), and
-    // each one holds its TMEM columns only for the row it solves.
-    const int64_t grid = std::min<int64_t>(a.nrows, (int64_t)INT32_MAX);
-    k_sweep_tc<<<(unsigned)grid, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
+    // many CTAs resident per SM as shared memory and registers allow (5), and
+    // each holds its 128 TMEM columns only from its Gram to the read-out.
+    // Exactly one row per CTA: a CTA allocates TMEM once (the allocation
+    // relinquishes the CTA's permit to allocate again).
+    if (a.nrows > (int64_t)INT32_MAX) {
+        als_set_error("sweep: more rows than CTAs in one launch");
+        return ALS_ENOTSUP;
+    }
+    k_sweep_tc<<<(unsigned)a.nrows, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
