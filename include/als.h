@@ -343,8 +343,8 @@ typedef struct {
     int32_t heavy_min;        /* default 512    */
     int32_t grid_mult;        /* default 32     */
     int32_t sweep_bin_min;    /* default 0      */
-    int32_t split_min;        /* default 4096   */
-    int32_t seg_len;          /* default 2048, >= 32 */
+    int32_t split_min;        /* default 16384  */
+    int32_t seg_len;          /* default 4096, >= 32 */
     int32_t gram_path;        /* in use         */
 } als_launch;
 

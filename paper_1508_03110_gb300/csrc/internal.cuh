@@ -100,8 +100,8 @@ struct als_ctx {
     std::vector<int64_t> h_beg[2];     // first rating of each row, in degree order (host)
 
     // heavy rows split into segments (a prefix of each side's degree order)
-    int split_min = 4096;              // rows with >= this many ratings are split
-    int seg_len = 2048;                // ratings per segment
+    int split_min = 16384;             // rows with >= this many ratings are split
+    int seg_len = 4096;                // ratings per segment
     int64_t nsplit[2] = {0, 0};        // split rows per side
     int64_t nseg[2] = {0, 0};          // segments per side
     int32_t *seg_row[2] = {nullptr, nullptr};
