@@ -1,24 +1,25 @@
 // Mixed-precision half sweep with the Gram matrices on the 5th-generation
 // tensor cores (tcgen05, sm_103a).
 //
-// For each row i (one CTA of 4 warps per row, 4 CTAs per SM), with the fixed
+// For each row i (one CTA of 4 warps per row, 5 CTAs per SM), with the fixed
 // side F (FP32 factor rows):
 //   1. gather: the row's ratings are taken 32 per chunk, a warp 8 of them;
 //      each rating's factor row f is read once, into registers, and split
-//      into hi = bf16(f) and lo2 = bf16(2 (f - hi)), stored into two
+//      into hi = bf16(f) and lo = bf16(f - hi), stored into two
 //      128-byte-swizzled, MN-major shared tiles H and L (rating k of the chunk
 //      is K index k, the factor index is the M/N index); the same FP32 values
 //      give the chunk's part of the first residual sum_e f_e (r_e - f_e . u0)
 //      at the current row u0 = x_i;
 //   2. Gram: one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//      M = 128, N = round_up(n_f, 16), K = 16 per instruction): D += H H^T
-//      and D += H L^T, so D = sum_e hi_e (hi_e + 2 lo_e)^T accumulates in
-//      TMEM; its symmetric part is sum_e (hi hi^T + hi lo^T + lo hi^T), the
-//      Gram matrix with ~2^-17 relative error (the lo lo^T term is dropped).
-//      Two stages: while the MMAs of one chunk run, the next chunk's rows are
-//      read and split; tcgen05.commit on an mbarrier releases a stage;
-//   3. tcgen05.ld moves D into FP32 shared memory (row m of D is TMEM lane
-//      m), A = (D + D^T)/2 + lambda n_i I;
+//      M = 128, N = round_up(n_f, 16), K = 16 per instruction): D += H H^T,
+//      D += H L^T and D += L H^T, so D = sum_e (hi hi^T + hi lo^T + lo hi^T)
+//      accumulates in TMEM: the Gram matrix with ~2^-17 relative error (the
+//      lo lo^T term is dropped), symmetric by construction.  Two stages:
+//      while the MMAs of one chunk run, the next chunk's rows are read and
+//      split; tcgen05.commit on an mbarrier releases a stage;
+//   3. tcgen05.ld moves D's lower triangle into packed FP32 shared memory
+//      (row m of D is TMEM lane m), A = D + lambda n_i I; the CTA then frees
+//      its TMEM columns, which it holds only from the Gram to this read-out;
 //   4. blocked Cholesky of A (inverted diagonal blocks) and the refinement of
 //      the ALS solve from u0: u <- u + A^{-1} res, res = sum_e f_e (r_e -
 //      f_e . u) - lambda n_i u in FP32 from the FP32 factors (the first

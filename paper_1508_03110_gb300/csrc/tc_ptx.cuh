@@ -1,6 +1,6 @@
 // Inline-PTX helpers for the Blackwell (sm_103a) tensor-core path: TMEM
 // allocation, tcgen05.mma issue/commit, tcgen05.ld, shared-memory matrix
-// descriptors, mbarriers with bounded waits, and cp.async gathers.
+// descriptors, mbarriers with bounded waits, and shared-memory stores.
 #pragma once
 
 #include <stdint.h>
@@ -42,20 +42,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
     return true;
 }
 
-// ---- cp.async (16 B, L2 only) -------------------------------------------------
+// ---- shared-memory stores ---------------------------------------------------
 __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
     asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16_zero(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // generic-proxy shared-memory writes -> visible to the async proxy (tensor core)
 __device__ __forceinline__ void fence_proxy_async_smem() {
