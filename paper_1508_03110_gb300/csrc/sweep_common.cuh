@@ -92,6 +92,31 @@ __device__ __forceinline__ void ld4f(const float *p, float (&v)[4]) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
+// d[q] <- sum of d[q] over the warp's 32 lanes, for 8 values at once: three
+// halving exchanges leave each lane one value summed over 8 lanes, two more
+// finish the sum over the warp, and 8 reads gather the totals (17 shuffles
+// instead of 40)
+__device__ __forceinline__ void warp_allsum8(float (&d)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float e4[4], e2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? d[i] : d[i + 4];
+        e4[i] = (b4 ? d[i + 4] : d[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? e4[i] : e4[i + 2];
+        e2[i] = (b3 ? e4[i + 2] : e4[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float e1 = (b2 ? e2[1] : e2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? e2[0] : e2[1], 4);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 2);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+    // lane l now holds the total of value 4 b4 + 2 b3 + b2
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = __shfl_sync(0xffffffffu, e1, ((q >> 2) & 1) * 16 + ((q >> 1) & 1) * 8 + (q & 1) * 4);
+}
+
 // acc += sum over q < 8 with 4 q < cnt of f_q (r_q - f_q . u), f_q the FP32
 // factor row of id ix[4 q] and r_q = vx[4 q]: the warp's share of the FP32
 // residual of the row's normal equations (lane = 4-wide slot of the row).
@@ -115,18 +140,17 @@ __device__ __forceinline__ void resid8(const float *F, int ld, const int32_t *ix
 #pragma unroll
         for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+    warp_allsum8(d, lane);
+    // the 8 terms in plain FP32, then one compensated add into the running sum
+    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (4 * q < cnt) {
-            const float er = r[q] - d[q];
+        const float er = 4 * q < cnt ? r[q] - d[q] : 0.0f;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
-        }
+        for (int i = 0; i < 4; ++i) cs[i] = fmaf(er, f[q][i], cs[i]);
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], cs[i]);
 }
 
 // Stopping test of the mixed form's refinement u <- u + Ahat^-1 (v - A u)

@@ -167,17 +167,19 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
 #pragma unroll
                         for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
                     }
+                    warp_allsum8(d, lane);
+                    {
+                        // the chunk's 8 terms in plain FP32, then one compensated
+                        // add into the row's running sum
+                        float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
+                        for (int q = 0; q < 8; ++q) {
+                            const float er = cj[q] >= 0 ? cr[q] - d[q] : 0.0f;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (cj[q] >= 0) {
-                            const float er = cr[q] - d[q];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], er * f[q][i]);
+                            for (int i = 0; i < 4; ++i) cs[i] = fmaf(er, f[q][i], cs[i]);
                         }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], cs[i]);
                     }
                     if (act) {
                         const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
@@ -191,12 +193,12 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
                             uint32_t hw[2], lw[2];
 #pragma unroll
                             for (int i = 0; i < 2; ++i) {
-                                const __nv_bfloat16 h0 = __float2bfloat16_rn(f[q][2 * i]);
-                                const __nv_bfloat16 h1 = __float2bfloat16_rn(f[q][2 * i + 1]);
-                                const __nv_bfloat16 l0 = __float2bfloat16_rn(f[q][2 * i] - __bfloat162float(h0));
-                                const __nv_bfloat16 l1 = __float2bfloat16_rn(f[q][2 * i + 1] - __bfloat162float(h1));
-                                hw[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                                lw[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                                const __nv_bfloat162 h = __floats2bfloat162_rn(f[q][2 * i], f[q][2 * i + 1]);
+                                const float2 hf = __bfloat1622float2(h);
+                                const __nv_bfloat162 l =
+                                    __floats2bfloat162_rn(f[q][2 * i] - hf.x, f[q][2 * i + 1] - hf.y);
+                                hw[i] = *reinterpret_cast<const uint32_t *>(&h);
+                                lw[i] = *reinterpret_cast<const uint32_t *>(&l);
                             }
                             st_shared_v2(stage + off, hw[0], hw[1]);
                             st_shared_v2(stage + TILE_BYTES + off, lw[0], lw[1]);
