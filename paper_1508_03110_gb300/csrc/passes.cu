@@ -120,6 +120,56 @@ __device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int6
     }
 }
 
+// d[q] <- sum of d[q] over the LPR-lane group, for 4 values at once; for a
+// whole warp (LPR == 32) two halving exchanges and three more leave each lane
+// one total and 4 reads gather them (10 shuffles instead of 20)
+template <int LPR, typename T>
+__device__ __forceinline__ void gsum4(T (&d)[4], unsigned mask, int lane) {
+    if constexpr (LPR == 32) {
+        const bool b4 = lane & 16, b3 = lane & 8;
+        T e2[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) e2[i] = (b4 ? d[i + 2] : d[i]) + __shfl_xor_sync(mask, b4 ? d[i] : d[i + 2], 16);
+        T e1 = (b3 ? e2[1] : e2[0]) + __shfl_xor_sync(mask, b3 ? e2[0] : e2[1], 8);
+        e1 += __shfl_xor_sync(mask, e1, 4);
+        e1 += __shfl_xor_sync(mask, e1, 2);
+        e1 += __shfl_xor_sync(mask, e1, 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = __shfl_sync(mask, e1, ((q >> 1) & 1) * 16 + (q & 1) * 8);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = gsum<LPR>(d[q], mask);
+    }
+}
+
+// acc (compensated in FP32) += sum over the 4 ratings e .. e + 3 of
+// f_e (r_e - x . f_e), f_e the gathered rows; all 4 rows are requested
+// before any is used
+template <typename T, int LPR>
+__device__ __forceinline__ void grad4(const PassArgs &a, const T *Xo, const T (&x)[4], int64_t e, int gl, int lane,
+                                      unsigned mask, bool act, T (&acc)[4], T (&cmp)[4]) {
+    T f[4][4], d[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t j = a.idx[e + q];
+        if (act) ld4(Xo + j * a.ld + 4 * gl, f[q]);
+        else zero4(f[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] = dot4(x, f[q]);
+    gsum4<LPR>(d, mask, lane);
+    T cs[4];
+    zero4(cs);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const T er = (T)a.val[e + q] - d[q];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cs[i] = fma(er, f[q][i], cs[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], cs[i]);
+}
+
 template <typename T, int LPR>
 __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
     const int lane = threadIdx.x & 31, gl = lane % LPR;
@@ -137,20 +187,7 @@ __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
         zero4(cmp);
         if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
         int64_t e = 0;
-        for (; e + 2 <= n; e += 2) {
-            const int64_t j0 = a.idx[beg + e], j1 = a.idx[beg + e + 1];
-            T f0[4], f1[4];
-            if (act) { ld4(Xo + j0 * a.ld + 4 * gl, f0); ld4(Xo + j1 * a.ld + 4 * gl, f1); }
-            else { zero4(f0); zero4(f1); }
-            T d0 = gsum<LPR>(dot4(x, f0), mask);
-            T d1 = gsum<LPR>(dot4(x, f1), mask);
-            const T e0 = (T)a.val[beg + e] - d0, e1 = (T)a.val[beg + e + 1] - d1;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                kadd(acc[i], cmp[i], e0 * f0[i]);
-                kadd(acc[i], cmp[i], e1 * f1[i]);
-            }
-        }
+        for (; e + 4 <= n; e += 4) grad4<T, LPR>(a, Xo, x, beg + e, gl, lane, mask, act, acc, cmp);
         for (; e < n; ++e) {
             const int64_t j0 = a.idx[beg + e];
             T f0[4];
@@ -185,7 +222,9 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
         zero4(acc);
         zero4(cmp);
         if (act) ld4(Xs + row * a.ld + 4 * gl, x); else zero4(x);
-        for (int64_t e = e0; e < e1; ++e) {
+        int64_t e = e0;
+        for (; e + 4 <= e1; e += 4) grad4<T, LPR>(a, Xo, x, e, gl, lane, mask, act, acc, cmp);
+        for (; e < e1; ++e) {
             const int64_t j = a.idx[e];
             T f[4];
             if (act) ld4(Xo + j * a.ld + 4 * gl, f); else zero4(f);
