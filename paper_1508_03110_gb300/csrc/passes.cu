@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "sweep_common.cuh"
 
 namespace {
 
@@ -308,6 +309,49 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
     }
 }
 
+// ratings [e, e1) of one row.  Mixed form with whole-warp groups: two
+// ratings per step, their four rows requested together and their eight dot
+// products all-reduced at once (17 shuffles instead of 40); otherwise one
+// rating at a time.
+template <typename T, int LPR, bool HAS_P>
+__device__ __forceinline__ void lscoef_range(const PassArgs &a, const T (&xu)[4], const T (&pu)[4], const T *Xo,
+                                             const T *Po, int64_t e, int64_t e1, int gl, int lane, bool act,
+                                             unsigned mask, int &owner, LsPending<T> &q, double (&t)[5]) {
+    if constexpr (sizeof(T) == 4 && LPR == 32 && HAS_P) {
+        for (; e + 2 <= e1; e += 2) {
+            const int64_t j0 = a.idx[e], j1 = a.idx[e + 1];
+            const float r0 = a.val[e], r1 = a.val[e + 1];
+            float xm0[4], pm0[4], xm1[4], pm1[4];
+            if (act) {
+                ld4(Xo + j0 * a.ld + 4 * gl, xm0);
+                ld4(Po + j0 * a.ld + 4 * gl, pm0);
+                ld4(Xo + j1 * a.ld + 4 * gl, xm1);
+                ld4(Po + j1 * a.ld + 4 * gl, pm1);
+            } else {
+                zero4(xm0); zero4(pm0); zero4(xm1); zero4(pm1);
+            }
+            float d[8] = {dot4(xu, xm0), dot4(xu, pm0), dot4(pu, xm0), dot4(pu, pm0),
+                          dot4(xu, xm1), dot4(xu, pm1), dot4(pu, xm1), dot4(pu, pm1)};
+            warp_allsum8(d, lane);
+            if (owner == gl) {
+                q.r = r0; q.d0 = d[0]; q.d1 = d[1]; q.d2 = d[2]; q.d3 = d[3];
+                q.have = true;
+            }
+            if (owner + 1 == gl) {
+                q.r = r1; q.d0 = d[4]; q.d1 = d[5]; q.d2 = d[6]; q.d3 = d[7];
+                q.have = true;
+            }
+            owner += 2;
+            if (owner == LPR) {
+                owner = 0;
+                ls_flush<T, HAS_P>(q, t);
+            }
+        }
+    }
+    for (; e < e1; ++e)
+        lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
+}
+
 template <int LPR>
 __device__ __forceinline__ void tsum5(double (&t)[5], unsigned mask) {
 #pragma unroll
@@ -367,8 +411,7 @@ __global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
         int owner = 0;
         LsPending<T> q;
         q.have = false;
-        for (int64_t e = beg; e < beg + n; ++e)
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
+        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, beg, beg + n, gl, lane, act, mask, owner, q, t);
         ls_flush<T, HAS_P>(q, t);
         tsum5<LPR>(t, mask);
         lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
@@ -400,8 +443,7 @@ __global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
         int owner = 0;
         LsPending<T> q;
         q.have = false;
-        for (int64_t e = e0; e < e1; ++e)
-            lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
+        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, e0, e1, gl, lane, act, mask, owner, q, t);
         ls_flush<T, HAS_P>(q, t);
         tsum5<LPR>(t, mask);
         if (gl == 0)
