@@ -541,7 +541,7 @@ def main():
     # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command
     # on this workload with the shapes the autotuner picks for it (no split
     # rows); other workloads have no capture
-    traffic = 8.05e8 if (args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
+    traffic = 8.04e8 if (args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
                          and launch["split_min"] > 33108) else None
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
