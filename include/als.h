@@ -338,6 +338,11 @@ ALS_API void als_server_destroy(als_server *srv);
  *                  mixed form rows of more than ~1e5 ratings need splitting
  *                  for accuracy, and the autotuner never goes above 65536)
  *   gram_path      ALS_GRAM_FMA or ALS_GRAM_TC (the latter ALS_MIXED only)
+ *   dual_max       tensor-core sweep (ALS_MIXED, lambda > 0): rows with at
+ *                  most min(dual_max, n_f) ratings are solved through their
+ *                  n_i x n_i matrix F F^T + lambda n_i I (Woodbury identity:
+ *                  the same solution of Eq. (4), from a factorisation of
+ *                  n_i^3 / 3 flops instead of n_f^3 / 3); 0..64, 0 = none
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t heavy_min;        /* default 512    */
@@ -346,6 +351,7 @@ typedef struct {
     int32_t split_min;        /* default 16384  */
     int32_t seg_len;          /* default 4096, >= 32 */
     int32_t gram_path;        /* in use         */
+    int32_t dual_max;         /* default 64     */
 } als_launch;
 
 ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);
@@ -364,8 +370,8 @@ typedef struct {
 
 /* Time candidate shapes on this context's own data, at its current factors
  * and direction, one parameter group at a time (pass threshold and grid cap;
- * Gram path where both apply; split threshold and segment length; FMA degree
- * bin), and keep the fastest.  No factor, direction or NCG state is modified.
+ * Gram path where both apply; split threshold and segment length; light-row
+ * bound of the tensor-core sweep; FMA degree bin), and keep the fastest.  No factor, direction or NCG state is modified.
  * reps (1..100): timed repetitions per candidate, best kept.  out may be
  * NULL. */
 ALS_API als_status als_autotune(als_ctx *ctx, int32_t reps, als_tune_report *out);

@@ -125,6 +125,8 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.notspd = c->dflags;
     a.timeout = c->dflags + 7;
     a.nbig = c->sweep_big[side];
+    a.ndual = c->sweep_dual[side];
+    a.dual_nmax = std::min(c->dual_max, c->nf);
     const int64_t H = c->nsplit[side];
     if (H == 0) return launch_sweep(c, a, c->f64, c->use_tc);
     // the heaviest rows, split across CTAs, on the side stream; the rest, one
@@ -591,6 +593,7 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
     if (s != ALS_OK) return fail(s);
     s = build_split(c);  // segment lists of the heaviest rows
     if (s != ALS_OK) return fail(s);
+    count_dual_rows(c);
     if (cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return fail(ALS_ECUDA); }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         als_set_error(std::string("als_create: ") + cudaGetErrorString(cudaGetLastError()));
@@ -1002,6 +1005,7 @@ void fill_launch(const als_ctx *c, als_launch *o) {
     o->split_min = c->split_min;
     o->seg_len = c->seg_len;
     o->gram_path = c->f64 ? ALS_GRAM_FMA : (c->use_tc ? ALS_GRAM_TC : ALS_GRAM_FMA);
+    o->dual_max = c->dual_max;
 }
 
 // apply launch shapes (validated by the caller); rebuilds what depends on them
@@ -1023,13 +1027,15 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
         c->seg_len = l.seg_len;
         if ((s = build_split(c)) != ALS_OK) return s;
     }
+    c->dual_max = l.dual_max;
+    count_dual_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
 }
 
 bool launch_valid(const als_ctx *c, const als_launch &l) {
     if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
-        l.seg_len < 32)
+        l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX)
         return false;
     if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
     if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
@@ -1047,7 +1053,7 @@ extern "C" als_status als_get_launch(als_ctx *c, als_launch *out) {
 extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
     if (!c || !in || !launch_valid(c, *in)) {
         als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
-                      "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form)");
+                      "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64)");
         return ALS_EINVAL;
     }
     return apply_launch(c, *in);
@@ -1118,6 +1124,14 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
             als_launch cand = cur;
             cand.split_min = sc[0];
             cand.seg_len = sc[1];
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+    }
+    if (!c->f64 && cur.gram_path == ALS_GRAM_TC && c->cfg.lambda > 0.0) {
+        // light-row solve through n_i x n_i matrices: the longest such row
+        for (int d : {0, 16, 32, 48, 64}) {
+            als_launch cand = cur;
+            cand.dual_max = d;
             if ((s = trial(cand, false, best)) != ALS_OK) return s;
         }
     }

@@ -232,10 +232,24 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
 
 }  // namespace
 
-als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a);  // sweep_tc.cu
+als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a);                // sweep_tc.cu
+als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax);    // sweep_dual.cu
 
 als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc) {
-    if (tc && !f64) return launch_sweep_tc(c, a);
+    if (tc && !f64) {
+        // the lightest rows (a suffix of the degree order) through their
+        // n_i x n_i matrix, the rest on the tensor cores
+        const int64_t nd = (a.order && !a.seg_out && a.dual_nmax > 0) ? std::min(a.ndual, a.nrows) : 0;
+        if (nd <= 0) return launch_sweep_tc(c, a);
+        SweepArgs h = a;
+        h.nrows = a.nrows - nd;
+        als_status s = launch_sweep_tc(c, h);
+        if (s != ALS_OK) return s;
+        SweepArgs l = a;
+        l.order = a.order + h.nrows;
+        l.nrows = nd;
+        return launch_sweep_dual(c, l, a.dual_nmax);
+    }
     if (a.nf <= 32) {
         // degree bin: the heaviest rows (a prefix of the degree order) get a
         // CTA each, the rest a warp each

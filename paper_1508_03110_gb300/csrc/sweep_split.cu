@@ -310,6 +310,7 @@ als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side) {
     // 1. segment partials
     SweepArgs b = a;
     b.nbig = 0;
+    b.ndual = 0;
     b.seg_row = c->seg_row[side];
     b.seg_beg = c->seg_beg[side];
     b.seg_len = c->seg_len_d[side];
