@@ -393,18 +393,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def sweep_flops(r, n_f, refine, precision):
-    """Algorithmic FLOPs of one ALS sweep (both halves), per the method:
-    symmetric Gram 2 * nnz * n_f (n_f + 1) (n_f (n_f+1)/2 FMAs per rating and
-    half), Cholesky n_f^3 / 3 and triangular solves 2 n_f^2 per row and solve,
-    the right-hand side (FP64) or the matrix-free residual (mixed, 4 n_f per
-    rating and refinement) per half."""
-    rows = r.n_u + r.n_m
-    gram = 2.0 * r.nnz * n_f * (n_f + 1)
-    chol = rows * n_f ** 3 / 3.0
+def sweep_flops(r, n_f, refine, precision, dual_max=0):
+    """Algorithmic FLOPs of one ALS sweep (both halves) as the kernels form
+    it; returns (total, the part on the tensor cores).
+
+    A row with d ratings solved through its n_f x n_f matrix: symmetric Gram
+    d n_f (n_f + 1) (n_f (n_f + 1) / 2 FMAs per rating), Cholesky n_f^3 / 3,
+    per refinement step the triangular solves 2 n_f^2 and the matrix-free
+    residual 4 n_f d (mixed; the FP64 form forms the right-hand side, 2 n_f d,
+    and solves once).  In the mixed tensor-core sweep a row with
+    0 < d <= min(dual_max, n_f) is solved through its d x d matrix F F^T:
+    n_f d (d + 1) for F F^T, d^3 / 3 for its Cholesky, and per refinement step
+    4 n_f d (F v and F^T z), 2 d^2 (solves) and the 4 n_f d residual.  Rows
+    without ratings cost nothing."""
+    d = np.concatenate([np.bincount(r.rows, minlength=r.n_u),
+                        np.bincount(r.cols, minlength=r.n_m)]).astype(np.float64)
+    T = min(dual_max, n_f) if (precision == "mixed" and r.lam > 0) else 0
+    light = (d > 0) & (d <= T)
+    full = d > 0
+    full &= ~light
+    dl, dh = d[light], d[full]
+    gram = float(np.sum(dh)) * n_f * (n_f + 1)
+    chol = float(full.sum()) * n_f ** 3 / 3.0
     if precision == "fp64":
-        return gram + chol + rows * 2 * n_f ** 2 + 2.0 * r.nnz * 2 * n_f
-    return gram + chol + refine * (rows * 2 * n_f ** 2 + 2.0 * r.nnz * 4 * n_f)
+        return gram + chol + float(full.sum()) * 2 * n_f ** 2 + float(np.sum(dh)) * 2 * n_f, 0.0
+    tc_rows = gram + chol + refine * (float(full.sum()) * 2 * n_f ** 2 + float(np.sum(dh)) * 4 * n_f)
+    light_rows = float(np.sum(n_f * dl * (dl + 1) + dl ** 3 / 3.0)) + \
+        refine * float(np.sum(8 * n_f * dl + 2 * dl ** 2))
+    return tc_rows + light_rows, gram
 
 
 def oracle_sample(r, x0, budget, rng_seed=0):
@@ -537,12 +553,14 @@ def main():
         tune = m.autotune(reps=2)
     launch = m.get_launch()
     m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
-    # DRAM bytes (read + write) of one sweep's two k_sweep_tc launches, from an
-    # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command
-    # on this workload with the shapes the autotuner picks for it (no split
-    # rows); other workloads have no capture
-    traffic = 8.04e8 if (args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
-                         and launch["split_min"] > 33108) else None
+    # DRAM bytes (read + write) of one sweep's launches (k_sweep_tc, and
+    # k_sweep_dual for the light rows), from an ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum) of this command on this
+    # workload without split rows, by light-row bound; other workloads and
+    # shapes have no capture
+    traffic = {0: 8.04e8, 64: 8.05e8}.get(launch.get("dual_max", 0)) if (
+        args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
+        and launch["split_min"] > 33108) else None
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
     sampler = ClockSampler(local)
@@ -573,20 +591,22 @@ def main():
     s1.record(stream)
     s1.synchronize()
     t_sweep = s0.elapsed_time(s1) / 1e3 / reps
-    fl = sweep_flops(r, r.n_f, args.refine, args.precision)
     use_tc = args.precision == "mixed" and launch["gram_path"] == 2
+    fl, gram = sweep_flops(r, r.n_f, args.refine, args.precision, launch.get("dual_max", 0) if use_tc else 0)
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     if use_tc:
-        # the dense contraction of the sweep is the Gram build: n_f (n_f + 1)
-        # flop per rating and half sweep (symmetric), two halves per sweep
-        gram = 2.0 * r.nnz * r.n_f * (r.n_f + 1)
+        # the dense contraction of the sweep is the Gram build of the rows
+        # solved through their n_f x n_f matrix: n_f (n_f + 1) flop per rating
+        # (symmetric); everything else (light rows' F F^T, Cholesky, solves,
+        # residuals) runs on the FP32 ALU
         peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
         achieved = gram / t_sweep / 1e12
         peak_note = f"bf16 dense, {peak_src} (burst)"
         alu_part = {"achieved": (fl - gram) / t_sweep / 1e12, "peak": fp32_peak,
                     "frac": (fl - gram) / t_sweep / 1e12 / fp32_peak,
-                    "what": "Cholesky, solves and FP32 residual (n_f^3/3 + 2 n_f^2 per row, 4 n_f per rating)"}
+                    "what": "Cholesky, solves, FP32 residuals, and the light rows' d x d matrices "
+                            "(n_f^3/3 + 2 n_f^2 per row, 4 n_f per rating; light rows n_f d (d+1) + d^3/3 + ...)"}
     else:
         alu_part = None
         if args.precision == "fp64":
@@ -598,8 +618,9 @@ def main():
         unit, bound = "TFLOP/s", "alu"
         achieved = fl / t_sweep / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per sweep (U + M launch), ncu",
-                "kernel": "k_sweep_tc (fused gather, tensor-core Gram, Cholesky, solves)" if use_tc
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per sweep (every launch of both halves), ncu",
+                "kernel": "k_sweep_tc + k_sweep_dual (fused gather, tensor-core Gram or light-row d x d matrix, "
+                          "Cholesky, solves)" if use_tc
                 else "k_sweep_fma (fused Gram, Cholesky, solves)",
                 "peak_source": peak_note, "sweep_ms": t_sweep * 1e3,
                 "what": "one sweep P(x): every launch of both half sweeps (split heavy rows included)"}
