@@ -60,6 +60,33 @@ def test_user_solve_is_ridge_least_squares():
         assert np.allclose(U[i], ref, rtol=1e-11, atol=1e-12)
 
 
+def test_light_rows_through_their_ratings_matrix():
+    """Reading 17 (Eq. (3) solved through the n_i x n_i matrix): for a row with
+    n_i < n_f ratings, the solution of Eq. (3) is F^T (F F^T + lambda n_i I)^-1 r,
+    and one correction of the mixed form's refinement from any u0,
+    u0 + (v - F^T G^-1 F v) / (lambda n_i) with v = F^T (r - F u0) - lambda n_i u0,
+    lands on it (Woodbury identity), all in FP64."""
+    P, x0 = _small_problem(n_u=40, n_m=25, n_f=12, dens=0.3, seed=3)
+    M = x0[P.n_u * P.n_f:].reshape(P.n_m, P.n_f)
+    U = oracle.half_sweep(P, 0, M).reshape(P.n_u, P.n_f)
+    rng = np.random.default_rng(5)
+    light = 0
+    for i in range(P.n_u):
+        a, b = P.uptr[i], P.uptr[i + 1]
+        n = b - a
+        if n == 0 or n >= P.n_f:
+            continue
+        light += 1
+        F, r, ln = M[P.uidx[a:b]], P.uval[a:b], P.lam * n
+        G = F @ F.T + ln * np.eye(n)
+        assert np.allclose(F.T @ np.linalg.solve(G, r), U[i], rtol=1e-10, atol=1e-13)
+        u0 = rng.normal(size=P.n_f)
+        v = F.T @ (r - F @ u0) - ln * u0
+        u1 = u0 + (v - F.T @ np.linalg.solve(G, F @ v)) / ln
+        assert np.allclose(u1, U[i], rtol=1e-9, atol=1e-12)
+    assert light >= 20
+
+
 def test_item_solve_is_ridge_least_squares():
     """Eq. (4), the item-side analogue."""
     P, x0 = _small_problem(seed=9)
