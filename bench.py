@@ -553,14 +553,11 @@ def main():
         tune = m.autotune(reps=2)
     launch = m.get_launch()
     m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
-    # DRAM bytes (read + write) of one sweep's launches (k_sweep_tc, and
-    # k_sweep_dual for the light rows), from an ncu capture
-    # (dram__bytes_read.sum + dram__bytes_write.sum) of this command on this
-    # workload without split rows, by light-row bound; other workloads and
-    # shapes have no capture
-    traffic = {0: 8.04e8, 64: 8.05e8}.get(launch.get("dual_max", 0)) if (
-        args.workload == "ml20m" and args.precision == "mixed" and launch["gram_path"] == 2
-        and launch["split_min"] > 33108) else None
+    # DRAM bytes (read + write) of one sweep's launches from an ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; none of
+    # the current sweep kernels (the prefetching variant of k_sweep_tc for rows
+    # of >= 256 ratings included) has been captured, so none is reported
+    traffic = None
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
     sampler = ClockSampler(local)

@@ -126,6 +126,7 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.timeout = c->dflags + 7;
     a.nbig = c->sweep_big[side];
     a.ndual = c->sweep_dual[side];
+    a.npf = c->sweep_pf[side];
     a.dual_nmax = std::min(c->dual_max, c->nf);
     const int64_t H = c->nsplit[side];
     if (H == 0) return launch_sweep(c, a, c->f64, c->use_tc);
@@ -593,7 +594,7 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
     if (s != ALS_OK) return fail(s);
     s = build_split(c);  // segment lists of the heaviest rows
     if (s != ALS_OK) return fail(s);
-    count_dual_rows(c);
+    count_sweep_rows(c);
     if (cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return fail(ALS_ECUDA); }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         als_set_error(std::string("als_create: ") + cudaGetErrorString(cudaGetLastError()));
@@ -1028,7 +1029,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
         if ((s = build_split(c)) != ALS_OK) return s;
     }
     c->dual_max = l.dual_max;
-    count_dual_rows(c);
+    count_sweep_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
 }

@@ -15,6 +15,7 @@
 #define ALS_TC_LD 128          // widest n_f of the tcgen05 Gram (one 128-row MMA tile)
 #define ALS_HEAVY_MIN 512      // rows at least this long get a whole CTA in the passes (default)
 #define ALS_DUAL_MAX 64        // longest row of the mixed form's light-row (n_i x n_i) solve
+#define ALS_TC_PF_MIN 256      // tensor-core sweep: rows at least this long prefetch their factor rows
 
 // Slots of the device scalar block (double S[]).
 enum {
@@ -100,6 +101,8 @@ struct als_ctx {
     int dual_max = ALS_DUAL_MAX;       // mixed tensor-core sweep: rows of <= min(dual_max, n_f) ratings
                                        // are solved through their n_i x n_i matrix (0: none)
     int64_t sweep_dual[2] = {0, 0};    // ... their count per side (a suffix of the degree order)
+    int64_t sweep_pf[2] = {0, 0};      // tensor-core sweep: rows of >= ALS_TC_PF_MIN ratings after the
+                                       // split rows (a prefix of the rest of the degree order)
     std::vector<int32_t> h_deg[2];     // degrees in degree order (host), filled on first use
     std::vector<int64_t> h_beg[2];     // first rating of each row, in degree order (host)
 
@@ -191,6 +194,7 @@ struct SweepArgs {
     int64_t nbig = 0;       // FMA sweep: the first nbig rows of `order` get a CTA each
     uint64_t wait_ns = 2000000000ull;  // limit of each bounded device wait
     int withhold = 0;       // self-test of the waits: no MMA is issued, so every wait runs out
+    int64_t npf = 0;        // tensor-core sweep: the first npf rows of `order` take the prefetching kernel
     // mixed tensor-core sweep: the last ndual rows of `order` (each with at
     // most dual_nmax <= ALS_DUAL_MAX ratings) take the light-row solve
     int64_t ndual = 0;
@@ -212,7 +216,8 @@ als_status launch_sweep(als_ctx *c, const SweepArgs &a, bool f64, bool tc);
 // for the current split_min / seg_len, then the split part of a half sweep
 als_status load_degrees(als_ctx *c);
 als_status build_split(als_ctx *c);
-void count_dual_rows(als_ctx *c);  // sweep_dual[] for the current dual_max, split rows and lambda
+// sweep_dual[] (for the current dual_max, split rows and lambda) and sweep_pf[]
+void count_sweep_rows(als_ctx *c);
 als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side);
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,12 @@
 //      residual comes from step 1).
 // Every mbarrier wait is bounded (%globaltimer): on expiry the CTA records a
 // timeout, frees its TMEM and returns.
+//
+// Heavy rows (and split-row segments) take the prefetching variant (PF): the
+// next chunk's factor rows are copied into a staging tile with cp.async
+// while the current chunk is split, stored and multiplied, so the gather's L2
+// latency is paid once per row rather than once per chunk.  The staging tile
+// costs 12.8 KB of shared memory (n_f = 100), i.e. 4 CTAs per SM instead of 5.
 #include "internal.cuh"
 #include "sweep_common.cuh"
 #include "tc_ptx.cuh"
@@ -42,10 +48,11 @@ constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
 constexpr int TMEM_COLS = 128;
 
 struct TcLayout {
-    int ring, A, vec, mbar, holder, total;
+    int ring, A, vec, mbar, holder, stg, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int nf) {
+// stg_ld > 0: a staging tile of KCH factor rows of stg_ld floats (PF variant)
+__host__ __device__ inline TcLayout tc_layout(int nf, int stg_ld = 0) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
@@ -56,11 +63,13 @@ __host__ __device__ inline TcLayout tc_layout(int nf) {
     L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
     L.mbar = L.vec + (5 * 128 + 1104) * 4;
     L.holder = L.mbar + 16;
-    L.total = L.holder + 16;
+    L.stg = L.holder + 16;
+    L.total = L.stg + KCH * stg_ld * 4;
     return L;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc) {
+template <bool PF>
+__global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a, int ntc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -68,8 +77,9 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
     const uint32_t sbase = raw + pad;
     const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const TcLayout L = tc_layout(nf);
+    const TcLayout L = tc_layout(nf, PF ? a.ld : 0);
     float *A = reinterpret_cast<float *>(base + L.A);
+    const float *stg = reinterpret_cast<const float *>(base + L.stg);
     float *vec = reinterpret_cast<float *>(base + L.vec);
     float *colk = vec, *v1 = vec + 128, *v2 = vec + 256, *u = vec + 384, *diag = vec + 512;
     float *part = vec + 640;   // residual partials (residual phase)
@@ -122,19 +132,34 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
             const int nch = (n + KCH - 1) / KCH;
             int pend[2] = {0, 0};
             // ids and ratings of this warp's ratings k = warp + 4 q (q < 8) of
-            // the next chunk, fetched one chunk ahead
-            int32_t nj[8];
-            float nr[8];
-            auto fetch = [&](int ch) {
+            // the next chunk, fetched one chunk ahead (PF: two ahead, the next
+            // chunk's rows being copied already)
+            int32_t nj[8], nnj[8];
+            float nr[8], nnr[8];
+            auto fetch = [&](int ch, int32_t (&oj)[8], float (&orr)[8]) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int64_t e = beg + (int64_t)ch * KCH + warp + 4 * q;
                     const bool in = ch < nch && e < beg + n;
-                    nj[q] = in ? a.idx[e] : -1;
-                    nr[q] = in ? a.val[e] : 0.0f;
+                    oj[q] = in ? a.idx[e] : -1;
+                    orr[q] = in ? a.val[e] : 0.0f;
                 }
             };
-            fetch(0);
+            // PF: copy the factor rows of ids jj into the staging tile (row k =
+            // warp + 4 q, this lane's 16 bytes: the lane later reads only those)
+            auto stage_rows = [&](const int32_t (&jj)[8]) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (jj[q] >= 0 && act)
+                        cp_async16(sbase + (uint32_t)L.stg + (uint32_t)(((warp + 4 * q) * a.ld + 4 * lane) * 4),
+                                   F + (int64_t)jj[q] * a.ld + 4 * lane);
+                cp_async_commit();
+            };
+            fetch(0, nj, nr);
+            if constexpr (PF) {
+                stage_rows(nj);
+                fetch(1, nnj, nnr);
+            }
             for (int ch = 0; ch < nch; ++ch) {
                 const int st = ch & 1;
                 if (pend[st]) {  // the MMAs of chunk ch-2 still read stage st
@@ -150,15 +175,29 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
                     cj[q] = nj[q];
                     cr[q] = nr[q];
                 }
-                fetch(ch + 1);
+                if constexpr (PF) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        nj[q] = nnj[q];
+                        nr[q] = nnr[q];
+                    }
+                    fetch(ch + 2, nnj, nnr);
+                } else {
+                    fetch(ch + 1, nj, nr);
+                }
                 // each factor row is read once, in FP32: it feeds the residual
                 // at u0 and, split into BF16 hi + lo, the operand tiles of stage st
                 {
                     float f[8][4];
+                    if constexpr (PF) cp_async_wait_all();  // this lane's copies of chunk ch
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        if (cj[q] >= 0 && act) ld4f(F + (int64_t)cj[q] * a.ld + 4 * lane, f[q]);
-                        else f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
+                        if (cj[q] >= 0 && act) {
+                            if constexpr (PF) ld4f(stg + (warp + 4 * q) * a.ld + 4 * lane, f[q]);
+                            else ld4f(F + (int64_t)cj[q] * a.ld + 4 * lane, f[q]);
+                        } else {
+                            f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
+                        }
                     }
                     float d[8];
 #pragma unroll
@@ -167,6 +206,10 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
 #pragma unroll
                         for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
                     }
+                    // PF: the staged rows are in registers now (the dot products
+                    // used them all): the next chunk's copies may overwrite them
+                    if constexpr (PF)
+                        if (ch + 1 < nch) stage_rows(nj);
                     warp_allsum8(d, lane);
                     {
                         // the chunk's 8 terms in plain FP32, then one compensated
@@ -222,6 +265,7 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
                 }
                 pend[st] = 1;
             }
+            if constexpr (PF) cp_async_wait_all();  // nothing in flight past the gather
             if (bail) break;
             for (int s = 0; s < 2; ++s) {
                 if (pend[s]) {
@@ -313,6 +357,30 @@ __global__ void __launch_bounds__(TC_THREADS, 5) k_sweep_tc(SweepArgs a, int ntc
     if (bail && t == 0) atomicAdd(a.timeout, 1);
 }
 
+template <bool PF>
+als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
+    if (a.nrows <= 0) return ALS_OK;
+    const TcLayout L = tc_layout(a.nf, PF ? a.ld : 0);
+    // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; PF ~54 KB: 4
+    size_t smem = (size_t)L.total + 1024;
+    if (raise_smem_limit((const void *)k_sweep_tc<PF>, smem) != ALS_OK) return ALS_ECUDA;
+    // the whole L1/shared array as shared memory, so that 5 CTAs fit per SM
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    // One CTA per row (rows in degree-descending order): the hardware keeps as
+    // many CTAs resident per SM as shared memory and registers allow, and
+    // each holds its 128 TMEM columns only from its Gram to the read-out.
+    // Exactly one row per CTA: a CTA allocates TMEM once (the allocation
+    // relinquishes the CTA's permit to allocate again).
+    if (a.nrows > (int64_t)INT32_MAX) {
+        als_set_error("sweep: more rows than CTAs in one launch");
+        return ALS_ENOTSUP;
+    }
+    k_sweep_tc<PF><<<(unsigned)a.nrows, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
 }  // namespace
 
 als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
@@ -322,23 +390,18 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
         return ALS_ENOTSUP;
     }
     const int ntc = (a.nf + 15) / 16 * 16;
-    const TcLayout L = tc_layout(a.nf);
-    // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM
-    size_t smem = (size_t)L.total + 1024;
-    if (raise_smem_limit((const void *)k_sweep_tc, smem) != ALS_OK) return ALS_ECUDA;
-    // the whole L1/shared array as shared memory, so that 5 CTAs fit per SM
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-    // One CTA per row (rows in degree-descending order): the hardware keeps as
-    // many CTAs resident per SM as shared memory and registers allow (5), and
-    // each holds its 128 TMEM columns only from its Gram to the read-out.
-    // Exactly one row per CTA: a CTA allocates TMEM once (the allocation
-    // relinquishes the CTA's permit to allocate again).
-    if (a.nrows > (int64_t)INT32_MAX) {
-        als_set_error("sweep: more rows than CTAs in one launch");
-        return ALS_ENOTSUP;
+    // split-row segments are long: all prefetching; otherwise the first npf
+    // rows of the order (the heaviest), then the rest
+    if (a.seg_out) return launch_tc<true>(c, a, ntc);
+    const int64_t npf = a.order ? std::max<int64_t>(0, std::min(a.npf, a.nrows)) : 0;
+    if (npf > 0) {
+        SweepArgs h = a;
+        h.nrows = npf;
+        als_status s = launch_tc<true>(c, h, ntc);
+        if (s != ALS_OK) return s;
     }
-    k_sweep_tc<<<(unsigned)a.nrows, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
-    ALS_CUDA_TRY(cudaGetLastError());
-    return ALS_OK;
+    SweepArgs l = a;
+    l.order = a.order ? a.order + npf : nullptr;
+    l.nrows = a.nrows - npf;
+    return launch_tc<false>(c, l, ntc);
 }
