@@ -19,8 +19,6 @@
 // memory once, into shared memory (row stride S floats, S / 4 odd, so that
 // 16-byte accesses of eight consecutive rows fall in distinct bank groups);
 // every later product with F, F^T and every later residual reads them there.
-#include <algorithm>
-
 #include "internal.cuh"
 #include "sweep_common.cuh"
 
@@ -299,29 +297,4 @@ als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
     k_sweep_dual<<<(unsigned)a.nrows, DU_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, nmax);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
-}
-
-// Rows of the light-row solve per side: those with at most min(dual_max, n_f)
-// ratings (a suffix of the degree-descending order), never a split row; none
-// in the FP64 form, past the tensor-core width, or without regularisation
-// (lambda = 0 leaves A singular for n_i < n_f, which the solve through G
-// would hide).  And the rows of the prefetching tensor-core kernel: those of
-// at least ALS_TC_PF_MIN ratings that are not split (a prefix of the order
-// once the split rows are taken off).
-void count_sweep_rows(als_ctx *c) {
-    for (int side = 0; side < 2; ++side) {
-        const std::vector<int32_t> &dd = c->h_deg[side];
-        const int64_t heavy =
-            std::partition_point(dd.begin(), dd.end(), [&](int32_t x) { return x >= ALS_TC_PF_MIN; }) - dd.begin();
-        c->sweep_pf[side] = std::max<int64_t>(0, heavy - c->nsplit[side]);
-        c->sweep_dual[side] = 0;
-        const int T = std::min(c->dual_max, c->nf);
-        if (c->f64 || T <= 0 || !(c->cfg.lambda > 0.0) || c->nf > ALS_TC_LD) continue;
-        const std::vector<int32_t> &d = c->h_deg[side];
-        const int64_t n = (int64_t)d.size();
-        if (n == 0) continue;
-        const int64_t first =
-            std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x > T; }) - d.begin();
-        c->sweep_dual[side] = std::max<int64_t>(0, std::min<int64_t>(n - first, n - c->nsplit[side]));
-    }
 }

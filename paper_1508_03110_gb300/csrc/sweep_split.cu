@@ -303,6 +303,29 @@ als_status build_split(als_ctx *c) {
     return ALS_OK;
 }
 
+// Rows of the light-row solve per side: those with at most min(dual_max, n_f)
+// ratings (a suffix of the degree-descending order), never a split row; none
+// in the FP64 form, past the tensor-core width, or without regularisation
+// (lambda = 0 leaves A singular for n_i < n_f, which the solve through G
+// would hide).  And the rows of the prefetching tensor-core kernel: those of
+// at least ALS_TC_PF_MIN ratings that are not split (a prefix of the order
+// once the split rows are taken off).
+void count_sweep_rows(als_ctx *c) {
+    for (int side = 0; side < 2; ++side) {
+        const std::vector<int32_t> &d = c->h_deg[side];
+        const int64_t n = (int64_t)d.size();
+        const int64_t heavy =
+            std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x >= ALS_TC_PF_MIN; }) - d.begin();
+        c->sweep_pf[side] = std::max<int64_t>(0, heavy - c->nsplit[side]);
+        c->sweep_dual[side] = 0;
+        const int T = std::min(c->dual_max, c->nf);
+        if (c->f64 || T <= 0 || !(c->cfg.lambda > 0.0) || c->nf > ALS_TC_LD || n == 0) continue;
+        const int64_t first =
+            std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x > T; }) - d.begin();
+        c->sweep_dual[side] = std::max<int64_t>(0, std::min<int64_t>(n - first, n - c->nsplit[side]));
+    }
+}
+
 als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side) {
     const int64_t H = c->nsplit[side], S = c->nseg[side];
     if (H == 0) return ALS_OK;
