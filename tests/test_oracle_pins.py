@@ -61,7 +61,7 @@ def test_user_solve_is_ridge_least_squares():
 
 
 def test_light_rows_through_their_ratings_matrix():
-    """Reading 17 (Eq. (3) solved through the n_i x n_i matrix): for a row with
+    """Eq. (3) solved through the n_i x n_i matrix of the row's ratings: for a row with
     n_i < n_f ratings, the solution of Eq. (3) is F^T (F F^T + lambda n_i I)^-1 r,
     and one correction of the mixed form's refinement from any u0,
     u0 + (v - F^T G^-1 F v) / (lambda n_i) with v = F^T (r - F u0) - lambda n_i u0,
@@ -372,3 +372,103 @@ def test_solve_rows_equals_half_sweep_rows():
     M = oracle.half_sweep(P, 1, x[:k]).reshape(P.n_m, P.n_f)
     assert np.array_equal(oracle.solve_rows(P, 0, x[k:], [3, 0, 29]), U[[3, 0, 29]])
     assert np.array_equal(oracle.solve_rows(P, 1, x[:k], [19, 2]), M[[19, 2]])
+
+
+# -- the fallback / restart branch of Algorithm 2 -------------------------------------
+# The paper does not say what Algorithm 2 does when the line search finds no
+# step.  The reading taken: x_{k+1} = xbar_k = P(x_k) (the ALS point, already
+# computed; it never raises f), and the next direction restarts with
+# beta = 0, i.e. p_{k+1} = -gbar_{k+1}.  These pins check that branch against
+# quantities recomputed from scratch (sweep, gradient, the ALS driver), never
+# against the ncg loop's own bookkeeping.
+
+def _check_fallback_records(P, x0, recs):
+    x_prev = np.array(x0, dtype=np.float64)
+    for r in recs:
+        assert r.fallback
+        assert r.alpha == 0.0 and r.beta == 0.0
+        xbar_prev = oracle.sweep(P, x_prev)
+        assert np.array_equal(r.x, xbar_prev), r.k          # x_{k+1} = P(x_k), exactly
+        xbar = oracle.sweep(P, r.x)
+        gbar = r.x - xbar
+        g = oracle.grad(P, r.x)
+        assert np.array_equal(r.state["xbar"], xbar)
+        assert np.array_equal(r.state["gbar"], gbar)
+        assert np.array_equal(r.state["p"], -gbar)           # restart: p_{k+1} = -gbar_{k+1}
+        assert r.state["s"] == float(gbar @ g)               # s_{k+1} = gbar_{k+1} . g_{k+1}
+        assert np.array_equal(r.g, g)
+        assert r.f <= oracle.loss(P, x_prev) * (1 + 1e-15)  # the ALS point never raises f
+        x_prev = r.x
+
+
+def test_failed_line_search_takes_the_als_point():
+    """Algorithm 3 with no admissible step (alpha0 so large that the Armijo
+    test fails, and no shrink allowed): every iteration takes the fallback,
+    so ALS-NCG must reproduce plain ALS (Algorithm 1) bit for bit."""
+    P, x0 = _small_problem(n_u=30, n_m=20, n_f=3, seed=11)
+    recs = oracle.alsncg(P, x0, 6, alpha0=1e6, max_shrinks=0)
+    _check_fallback_records(P, x0, recs)
+    als = oracle.als(P, x0, 6)
+    for r, a in zip(recs, als):
+        assert np.array_equal(r.x, a.x)
+        assert r.f == a.f
+
+
+def test_non_descent_direction_takes_the_preconditioner_point():
+    """c1 = g^T p >= 0 (p not a descent direction): no alpha is tried at all,
+    the step is x_{k+1} = xbar_k and the direction restarts.  A preconditioner
+    that points uphill, xbar = x + (x - P(x)), makes every p_k = -gbar_k an
+    ascent direction."""
+    P, x0 = _small_problem(n_u=30, n_m=20, n_f=3, seed=12)
+    uphill = lambda x: x + (x - oracle.sweep(P, x))          # noqa: E731
+    seen = []
+
+    def step(x, p, g):
+        c = oracle.ls_coeffs(P, x, p)
+        assert c[1] == pytest.approx(float(g @ p), rel=1e-10)
+        assert c[1] > 0.0
+        ls = oracle.backtracking(c)
+        seen.append(ls)
+        return ls
+
+    states = []
+    x_prev = np.array(x0)
+    out = oracle.ncg(x0, lambda x: oracle.grad(P, x), uphill, step, 4,
+                     on_iter=lambda k, x, g, info: states.append((x.copy(), g.copy(), info)))
+    assert all(not ls.ok and ls.shrinks == 0 for ls in seen)
+    for x, g, info in states:
+        assert info["fallback"] and info["beta"] == 0.0
+        assert np.array_equal(x, uphill(x_prev))            # x_{k+1} = xbar_k
+        gbar = x - uphill(x)
+        assert np.array_equal(info["state"]["p"], -gbar)
+        assert info["state"]["s"] == float(gbar @ g)
+        assert np.array_equal(g, oracle.grad(P, x))
+        x_prev = x
+    assert np.array_equal(out, x_prev)
+
+
+def test_fallback_then_resume_restarts_beta():
+    """A run where some steps pass and some fall back (at most 2 shrinks):
+    after every fallback the next direction is -gbar (beta = 0), after every
+    accepted step beta follows Eq. (8) from recomputed vectors."""
+    P, x0 = _small_problem(n_u=40, n_m=25, n_f=4, seed=13)
+    recs = oracle.alsncg(P, x0, 25, max_shrinks=2)
+    kinds = {r.fallback for r in recs}
+    assert kinds == {True, False}, "the case must contain both branches"
+    g_prev = oracle.grad(P, x0)
+    gbar_prev = x0 - oracle.sweep(P, x0)
+    p_prev = -gbar_prev
+    x_prev = np.array(x0)
+    for r in recs:
+        if r.fallback:
+            assert np.array_equal(r.x, oracle.sweep(P, x_prev))
+            assert r.beta == 0.0
+        else:
+            assert np.allclose(r.x, x_prev + r.alpha * p_prev, rtol=0, atol=1e-14 * np.abs(r.x).max())
+        gbar = r.x - oracle.sweep(P, r.x)
+        g = oracle.grad(P, r.x)
+        beta = 0.0 if r.fallback else float(gbar @ (g - g_prev)) / float(gbar_prev @ g_prev)
+        assert r.beta == pytest.approx(beta, rel=1e-12, abs=1e-300)
+        p = -gbar + beta * p_prev
+        assert np.allclose(r.state["p"], p, rtol=0, atol=1e-12 * np.abs(p).max())
+        x_prev, g_prev, gbar_prev, p_prev = r.x, g, gbar, r.state["p"]
