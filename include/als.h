@@ -30,7 +30,11 @@
  * Errors.  Every call returns an als_status; on failure the context stays
  *   valid, the iterate is unchanged, and als_last_error() returns a
  *   thread-local message.  Nothing throws across the ABI.  A failed CUDA call
- *   returns ALS_ECUDA.
+ *   returns ALS_ECUDA.  ALS_ETIMEOUT (a bounded device wait of the
+ *   tensor-core sweep ran out) is reported once, by the first call that
+ *   returns host values afterwards: what was computed since the last
+ *   successful such call is not valid, and the context runs again once a
+ *   checkpoint is restored (als_set_state) or new factors are set.
  * Precision.  ALS_FP64 computes everything in double (parity form).
  *   ALS_MIXED stores factors and NCG vectors in float, builds the Gram
  *   matrices in BF16 on the tensor cores (n_f > 64) or in FP32 (n_f <= 64),
@@ -241,7 +245,9 @@ ALS_API als_status als_linesearch_coeffs(als_ctx *ctx, const void *p_or_null, in
  * process exits; it limits n_u + n_m to 262,144 (ALS_EINVAL beyond).  The
  * first call on each device looks up that array's device address (a one-time
  * set-up, not an allocation): make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race on
+ * capture.  The address is kept per device together with the CUDA context
+ * it belongs to; after cudaDeviceReset the next call repeats the set-up
+ * (again: outside any capture).  All calls share the array: calls that overlap on the GPU race on
  * it and give wrong results; order them (one stream).  Nothing here calls
  * cudaMalloc, cudaFree or any allocating routine. */
 ALS_API als_status als_linesearch_coeffs_static(int64_t n_u, int64_t n_m, int32_t n_f, int32_t ld,
@@ -393,11 +399,44 @@ ALS_API als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter, do
  * limit_s (0 < limit_s <= 10): each CTA records the expiry, frees its TMEM
  * and returns, with nothing left in flight.  Returns ALS_ETIMEOUT when the
  * waits ran out as designed (*expired = CTAs that gave up, one per user row
- * with ratings); the context stays usable: its flags are cleared and its
- * factors and NCG state are untouched (only scratch is written).
+ * with ratings).  Its factors and NCG state are untouched (only scratch is
+ * written), and the expiry stays recorded as a real one inside a sweep
+ * would be: the next call that returns host values reports ALS_ETIMEOUT once
+ * and clears it, and als_set_state / als_set_factors clear it as well.
  * ALS_ENOTSUP unless the context uses the tensor-core Gram.  Note that
  * n_u x limit_s / (4 x SMs) seconds pass: use a small problem. */
 ALS_API als_status als_selftest_wait_expiry(als_ctx *ctx, double limit_s, int64_t *expired);
+
+/* Per-kernel timing of one sweep P(x) (no counterpart in the paper: the
+ * measurement behind the roofline figures).  Runs `reps` sweeps (1..1000)
+ * that write xbar = P(x) and gbar = x - xbar, which is what they hold between
+ * ALS-NCG iterations (x itself is not changed), with a CUDA event pair around
+ * every sweep launch on the stream it is launched on.  Classes (index):
+ *   0 k_sweep_tc, prefetching variant (rows of >= 256 ratings)
+ *   1 k_sweep_tc, the other tensor-core rows
+ *   2 k_sweep_dual, the light rows (solved through their n_i x n_i matrix)
+ *   3 k_sweep_fma (FP64 form, or FP32 Gram for small n_f)
+ *   4 the split heavy rows (segment partials, sums, solves; side stream)
+ * Per class: the summed launch durations per sweep (ms), the launches, rows
+ * and ratings one sweep gives it (both halves).  sweep_ms: the whole sweep,
+ * events on the context's stream.  Synchronous. */
+typedef struct {
+    double sweep_ms;
+    double ms[5];
+    int64_t rows[5];
+    int64_t ratings[5];
+    int32_t launches[5];
+} als_sweep_timing;
+ALS_API als_status als_time_sweep(als_ctx *ctx, int32_t reps, als_sweep_timing *out);
+
+/* Measured plain-ALU peaks of the current device (no counterpart in the
+ * paper: the denominators of the roofline fractions of the work that runs on
+ * the FMA pipes -- the sweep's Cholesky, solves and residuals).  A kernel of
+ * eight independent FMA chains per thread fills every SM; it is timed with
+ * CUDA events on a stream of its own (best of three, after a warm-up), about
+ * 0.1 s in all.  Outputs (either may be NULL): dense FMA TFLOP/s in FP32 and
+ * in FP64 (2 flop per FMA).  Synchronous. */
+ALS_API als_status als_probe_alu_peaks(double *fp32_tflops, double *fp64_tflops);
 
 /* Wait for all work enqueued by this context. */
 ALS_API als_status als_sync(als_ctx *ctx);

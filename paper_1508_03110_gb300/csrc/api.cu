@@ -224,7 +224,14 @@ als_status read_scalars(als_ctx *c) {
     ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->hflags[7]) {
-        als_set_error("a bounded device wait of the tensor-core sweep expired; results are not valid");
+        // reported once: the flag is cleared here, so that the context runs
+        // again after the caller restores a checkpoint (als_set_state) or
+        // sets new factors; what was computed since the expiry is not valid
+        c->hflags[7] = 0;
+        ALS_CUDA_TRY(cudaMemsetAsync(c->dflags + 7, 0, sizeof(int), c->stream));
+        ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        als_set_error("a bounded device wait of the tensor-core sweep expired; results since the last "
+                      "successful call are not valid: restore a checkpoint (als_set_state) or set new factors");
         return ALS_ETIMEOUT;
     }
     return ALS_OK;
@@ -632,6 +639,8 @@ extern "C" als_status als_set_factors(als_ctx *c, const void *U, const void *M, 
     ALS_CUDA_TRY(cudaMemcpyAsync(c->tmpvec, M, (size_t)c->n_m * c->nf * es, kind, c->stream));
     s = launch_convert_in(c, mblk(c, c->X), c->tmpvec, c->n_m, dtype, c->nf);
     if (s != ALS_OK) return s;
+    // new factors: an unreported expiry of a bounded wait no longer matters
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags + 7, 0, sizeof(int), c->stream));
     if (!on_device) ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->ncg_ready = false;
     c->k = 0;
@@ -704,6 +713,8 @@ extern "C" als_status als_set_state(als_ctx *c, const void *x, const void *p, co
     ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_GG0, &hs[1], sizeof(double), cudaMemcpyHostToDevice, c->stream));
     ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_NFALL, &hs[2], sizeof(double), cudaMemcpyHostToDevice, c->stream));
     ALS_CUDA_TRY(cudaMemcpyAsync(c->S + S_MODE, &hs[3], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // a restored checkpoint replaces whatever an expired bounded wait left
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags + 7, 0, sizeof(int), c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->k = (int64_t)scalars[2];
     c->ncg_ready = true;
@@ -1212,7 +1223,8 @@ extern "C" als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter,
 // Self-test of the bounded device waits: one half sweep of the tensor-core
 // kernel in which no MMA is issued and nothing signals the mbarriers, so every
 // CTA's wait runs out after limit_s; each records the expiry, frees its TMEM
-// and returns.  Nothing is left in flight; the flags are cleared afterwards.
+// and returns.  Nothing is left in flight; the expiry stays recorded in the
+// context as a real one would be.
 
 extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64_t *expired) {
     if (!c || !(limit_s > 0.0) || limit_s > 10.0) {
@@ -1248,7 +1260,11 @@ extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64
     ALS_CUDA_TRY(cudaMemcpyAsync(c->hflags, c->dflags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     const int64_t n = c->hflags[7];
-    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags, 0, 16 * sizeof(int), c->stream));
+    // the expiry stays recorded, as after a real one inside a sweep: the next
+    // call that reads the context's status reports ALS_ETIMEOUT once, and
+    // als_set_state / als_set_factors clear it; the other flags are reset
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags, 0, 7 * sizeof(int), c->stream));
+    ALS_CUDA_TRY(cudaMemsetAsync(c->dflags + 8, 0, 8 * sizeof(int), c->stream));
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (expired) *expired = n;
     if (n == 0) {
@@ -1257,4 +1273,108 @@ extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64
     }
     als_set_error("als_selftest_wait_expiry: the bounded waits ran out as designed");
     return ALS_ETIMEOUT;
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel-class timing of one sweep (events on each launch's own stream).
+
+void kt_begin(als_ctx *c, int cls, cudaStream_t st) {
+    KTimer *k = c->kt;
+    if (!k || k->depth > 0 || k->n[cls] >= KTimer::kMax) return;
+    cudaEventRecord(k->ev[cls][k->n[cls]][0], st);
+}
+
+void kt_end(als_ctx *c, int cls, cudaStream_t st) {
+    KTimer *k = c->kt;
+    if (!k || k->depth > 0 || k->n[cls] >= KTimer::kMax) return;
+    cudaEventRecord(k->ev[cls][k->n[cls]][1], st);
+    k->n[cls] += 1;
+}
+
+extern "C" als_status als_time_sweep(als_ctx *c, int32_t reps, als_sweep_timing *out) {
+    if (!c || !out || reps < 1 || reps > 1000) {
+        als_set_error("als_time_sweep: bad argument (1 <= reps <= 1000, out not NULL)");
+        return ALS_EINVAL;
+    }
+    als_status s = load_degrees(c);
+    if (s != ALS_OK) return s;
+    std::memset(out, 0, sizeof *out);
+    // rows and ratings of each class, from the degree order: split rows first,
+    // then (tensor-core sweep) the prefetching rows, the other tensor-core
+    // rows and the light rows; or (FMA sweep) every other row
+    const bool tc = c->use_tc && !c->f64;
+    for (int side = 0; side < 2; ++side) {
+        const std::vector<int32_t> &d = c->h_deg[side];
+        const int64_t n = (int64_t)d.size();
+        const int64_t H = c->nsplit[side];
+        auto add = [&](int cls, int64_t b, int64_t e) {
+            b = std::max<int64_t>(0, std::min(b, n));
+            e = std::max<int64_t>(b, std::min(e, n));
+            out->rows[cls] += e - b;
+            for (int64_t r = b; r < e; ++r) out->ratings[cls] += d[r];
+        };
+        add(KT_SPLIT, 0, H);
+        if (tc) {
+            const int64_t npf = std::min(c->sweep_pf[side], n - H);
+            const int64_t nd = std::min(c->sweep_dual[side], n - H);
+            add(KT_TC_PF, H, H + npf);
+            add(KT_TC, H + npf, n - nd);
+            add(KT_DUAL, n - nd, n);
+        } else {
+            add(KT_FMA, H, n);
+        }
+    }
+    KTimer kt;
+    std::memset(&kt, 0, sizeof kt);
+    for (int a = 0; a < KT_NCLASS; ++a)
+        for (int i = 0; i < KTimer::kMax; ++i)
+            for (int j = 0; j < 2; ++j)
+                if (cudaEventCreate(&kt.ev[a][i][j]) != cudaSuccess) {
+                    als_set_error("als_time_sweep: cudaEventCreate failed");
+                    kt.ev[a][i][j] = nullptr;
+                }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto cleanup = [&]() {
+        c->kt = nullptr;
+        for (int a = 0; a < KT_NCLASS; ++a)
+            for (int i = 0; i < KTimer::kMax; ++i)
+                for (int j = 0; j < 2; ++j)
+                    if (kt.ev[a][i][j]) cudaEventDestroy(kt.ev[a][i][j]);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    // x is not changed: xbar = P(x) and gbar = x - xbar are written, which is
+    // what they already hold between ALS-NCG iterations (the kernels are
+    // deterministic)
+    for (int rep = 0; rep < reps; ++rep) {
+        for (int a = 0; a < KT_NCLASS; ++a) kt.n[a] = 0;
+        c->kt = &kt;
+        cudaEventRecord(e0, c->stream);
+        s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+        cudaEventRecord(e1, c->stream);
+        c->kt = nullptr;
+        if (s != ALS_OK) { cleanup(); return s; }
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            als_set_error(std::string("als_time_sweep: ") + cudaGetErrorString(e));
+            return ALS_ECUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out->sweep_ms += ms / reps;
+        for (int a = 0; a < KT_NCLASS; ++a) {
+            out->launches[a] = kt.n[a];
+            for (int i = 0; i < kt.n[a]; ++i) {
+                float m = 0.f;
+                cudaEventElapsedTime(&m, kt.ev[a][i][0], kt.ev[a][i][1]);
+                out->ms[a] += m / reps;
+            }
+        }
+    }
+    cleanup();
+    ALS_CUDA_TRY(cudaGetLastError());
+    return read_scalars(c);
 }

@@ -176,12 +176,20 @@ __global__ void __launch_bounds__(256) k_reduce_static(StaticArgs a) {
     if (threadIdx.x == 0) s->ticket = 0u;
 }
 
-// device address of g_scratch, looked up once per device (host code must not
-// pass the symbol itself: on the host it is only a stand-in)
+// device address of g_scratch, looked up once per device and CUDA context
+// (host code must not pass the symbol itself: on the host it is only a
+// stand-in).  The context handle is recorded beside the address: after
+// cudaDeviceReset the device's primary context is a new one, the module is
+// loaded again, and the array may sit elsewhere, so a changed handle means
+// the lookup is done again.
 constexpr int kMaxDevices = 64;
+typedef int (*CtxGetCurrentFn)(void **);
 std::mutex g_mu;
 StaticScratch *g_addr[kMaxDevices] = {};
+void *g_ctx[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_get = nullptr;
+bool g_ctx_get_tried = false;
 
 als_status scratch_for_device(StaticScratch **out, int *sms) {
     int dev = 0;
@@ -191,12 +199,27 @@ als_status scratch_for_device(StaticScratch **out, int *sms) {
         return ALS_ENOTSUP;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_ctx_get_tried) {
+        g_ctx_get_tried = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+        cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    if (g_ctx_get && g_ctx_get(&ctx) != 0) ctx = nullptr;
+    if (!g_addr[dev] || ctx != g_ctx[dev]) {
         void *p = nullptr;
         ALS_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch));
         int n = 0;
         ALS_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        // the lookup made the device's primary context current if it was not
+        if (g_ctx_get && g_ctx_get(&ctx) != 0) ctx = nullptr;
         g_addr[dev] = reinterpret_cast<StaticScratch *>(p);
+        g_ctx[dev] = ctx;
         g_sms[dev] = n;
     }
     *out = g_addr[dev];

@@ -24,8 +24,10 @@
 //      the ALS solve from u0: u <- u + A^{-1} res, res = sum_e f_e (r_e -
 //      f_e . u) - lambda n_i u in FP32 from the FP32 factors (the first
 //      residual comes from step 1).
-// Every mbarrier wait is bounded (%globaltimer): on expiry the CTA records a
-// timeout, frees its TMEM and returns.
+// Every mbarrier wait is bounded (%globaltimer): on expiry the CTA gives each
+// stage whose MMAs may still be in flight one more bounded wait, records a
+// timeout, frees its TMEM and returns.  The rows of such a launch are not
+// valid; the host reports the expiry once.
 //
 // Heavy rows (and split-row segments) take the prefetching variant (PF): the
 // next chunk's factor rows are copied into a staging tile with cp.async
@@ -266,16 +268,27 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                 pend[st] = 1;
             }
             if constexpr (PF) cp_async_wait_all();  // nothing in flight past the gather
-            if (bail) break;
-            for (int s = 0; s < 2; ++s) {
-                if (pend[s]) {
-                    const bool w = mbar_wait_bounded(mbar[s], phase[s], a.wait_ns);
-                    if (__syncthreads_or(!w)) { bail = true; break; }
-                    phase[s] ^= 1u;
-                    pend[s] = 0;
+            if (!bail) {
+                for (int s = 0; s < 2; ++s) {
+                    if (pend[s]) {
+                        const bool w = mbar_wait_bounded(mbar[s], phase[s], a.wait_ns);
+                        if (__syncthreads_or(!w)) { bail = true; break; }
+                        phase[s] ^= 1u;
+                        pend[s] = 0;
+                    }
                 }
             }
-            if (bail) break;
+            if (bail) {
+                // a wait ran out: the MMAs of a stage may still be reading this
+                // CTA's shared tiles and writing its TMEM, so every stage still
+                // pending gets one more bounded wait before the teardown frees
+                // the columns (the self-test issued none: nothing to wait for)
+                if (t == 0 && !a.withhold)
+                    for (int s = 0; s < 2; ++s)
+                        if (pend[s]) (void)mbar_wait_bounded(mbar[s], phase[s], a.wait_ns);
+                __syncthreads();
+                break;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i] - cmp[i];
             tc_fence_after();
@@ -376,7 +389,10 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
         als_set_error("sweep: more rows than CTAs in one launch");
         return ALS_ENOTSUP;
     }
-    k_sweep_tc<PF><<<(unsigned)a.nrows, TC_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, ntc);
+    cudaStream_t st = a.stream ? a.stream : c->stream;
+    kt_begin(c, PF ? KT_TC_PF : KT_TC, st);
+    k_sweep_tc<PF><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc);
+    kt_end(c, PF ? KT_TC_PF : KT_TC, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
