@@ -18,9 +18,16 @@ roofline = the fused sweep kernel (the dominant launch) against the measured
          peak of the unit that bounds it;
 cpu_baseline = the FP64 oracle on the host cores, on a bounded sample.
 
+s_to_tol = seconds (device work of the iterations, each context autotuned
+         before its clock starts) from the same x_0 to a relative gradient
+         norm |g_k| / |g_0|: mixed ALS-NCG and FP64 ALS-NCG to 1e-5 (mixed
+         also to 1e-6), plain FP64 ALS to 1e-3 (its |g| evaluations are not
+         timed, as in the paper), with (1/N)|g_k| of the paper's stopping
+         test beside each figure.
+
 `--impl reference` times the oracle alone (the reference arm of this build).
 Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N` runs N independent
-replicas (the method needs no exchange on one GPU), value is
+replicas (one problem fits one GPU and a replica needs no exchange); value is
 the sum over ranks and the time the max over ranks.
 """
 import argparse
@@ -56,8 +63,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 sweep timing")
+    ap.add_argument("--no-s2t", action="store_true", help="skip the seconds-to-tolerance runs")
+    ap.add_argument("--s2t-budget", type=float, default=90.0,
+                    help="seconds of iterations per method in the default run's s_to_tol")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "s_to_tol", "serving", "batched", "scale"])
+    ap.add_argument("--mode", default="throughput",
+                    choices=["throughput", "s_to_tol", "serving", "batched", "scale", "sweep_once"])
     ap.add_argument("--scale-steps", default="1e7,3e7,1e8,3e8,1e9", help="scale: ratings steps")
     ap.add_argument("--scale-nf", default="10,50", help="scale: n_f values")
     ap.add_argument("--n-prob", type=int, default=64, help="batched: number of problems")
@@ -73,48 +84,46 @@ def parse():
 TOLS = (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
 
 
-def run_s_to_tol(args):
-    """Seconds to reach |g_k| / |g_0| <= tol from the same x_0: mixed ALS-NCG,
-    FP64 ALS-NCG and plain FP64 ALS (Algorithm 1; as in the paper, the time
-    spent evaluating |g| for ALS is excluded).  Each context is autotuned
-    once before its clock starts.  Each method stops at the
-    tolerance or after `budget` seconds of its own iterations."""
+def s_to_tol_methods(r, x0, plan, budget, stream):
+    """Seconds from x_0 to |g_k| / |g_0| <= each tolerance of `plan`
+    (method -> its tolerances): mixed ALS-NCG, FP64 ALS-NCG and plain FP64
+    ALS (Algorithm 1; as in the paper, the time spent evaluating |g| for ALS is
+    excluded).  Each context is autotuned once before its clock starts; a
+    method stops at its tightest tolerance or after `budget` seconds of its
+    own iterations.  Returns method -> {reached, final, trajectory}; every
+    figure carries |g|/|g_0| and the paper's (1/N)|g| (N = n_f (n_u + n_m))."""
     import torch
-    import synth
     from paper_1508_03110_gb300 import ALS
 
-    r = synth.make_config(args.workload)
-    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
-    stream = torch.cuda.Stream()
-    out = {"mode": "s_to_tol", "workload": workload_name(args, r), "tol": args.tol,
-           "budget_s": args.budget, "methods": {}}
+    N = r.n_f * (r.n_u + r.n_m)
 
-    def ncg(prec):
+    def ncg(prec, tol):
         m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision=prec, stream=stream)
         m.set_x(x0)
         m.autotune(reps=1)  # setup, like the ratings builder: not timed
         traj, elapsed, k = [], 0.0, 0
         step = 10 if prec == "mixed" else 2
-        while elapsed < args.budget:
+        g0 = None
+        while elapsed < budget:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = m.run(step, args.tol, check_every=step)
+            info = m.run(step, tol, check_every=step)
             elapsed += time.perf_counter() - t0
             k += info["iters"]
-            rel = info["gnorm"] / info["gnorm0"]
-            traj.append((k, elapsed, rel))
-            if rel <= args.tol:
+            g0 = info["gnorm0"]
+            traj.append((k, elapsed, info["gnorm"] / g0, info["gnorm"] / N))
+            if info["gnorm"] / g0 <= tol:
                 break
         m.close()
         return traj
 
-    def als64():
+    def als64(tol):
         m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision="fp64", stream=stream)
         m.set_x(x0)
         m.autotune(reps=1)
         _, g0 = m.grad(want_vector=False)
         traj, elapsed, k = [], 0.0, 0
-        while elapsed < args.budget:
+        while elapsed < budget:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             m.sweep(5)
@@ -122,27 +131,66 @@ def run_s_to_tol(args):
             elapsed += time.perf_counter() - t0
             k += 5
             _, gn = m.grad(want_vector=False)          # not timed (as in the paper)
-            traj.append((k, elapsed, gn / g0))
-            if gn / g0 <= args.tol:
+            traj.append((k, elapsed, gn / g0, gn / N))
+            if gn / g0 <= tol:
                 break
         m.close()
         return traj
 
-    for name, fn in (("mixed_alsncg", lambda: ncg("mixed")), ("fp64_alsncg", lambda: ncg("fp64")),
-                     ("fp64_als", als64)):
-        if name not in args.methods.split(","):
-            continue
-        traj = fn()
+    out = {}
+    runners = {"mixed_alsncg": lambda t: ncg("mixed", t), "fp64_alsncg": lambda t: ncg("fp64", t),
+               "fp64_als": als64}
+    for name, tols in plan.items():
+        traj = runners[name](min(tols))
         first = {}
-        for tol in TOLS:
-            hit = [(k, t) for k, t, rel in traj if rel <= tol]
-            first[f"{tol:g}"] = {"iters": hit[0][0], "s": hit[0][1]} if hit else None
-        out["methods"][name] = {"reached": first, "final": {"iters": traj[-1][0], "s": traj[-1][1],
-                                                            "gnorm_rel": traj[-1][2]},
-                                "trajectory": traj[:: max(1, len(traj) // 40)]}
-        print(json.dumps({name: out["methods"][name]["reached"], "final": out["methods"][name]["final"]}),
-              file=sys.stderr, flush=True)
+        for tol in tols:
+            hit = [(k, t, gn) for k, t, rel, gn in traj if rel <= tol]
+            first[f"{tol:g}"] = {"iters": hit[0][0], "s": hit[0][1], "gnorm_over_N": hit[0][2]} if hit else None
+        out[name] = {"reached": first, "final": {"iters": traj[-1][0], "s": traj[-1][1],
+                                                 "gnorm_rel": traj[-1][2], "gnorm_over_N": traj[-1][3]},
+                     "trajectory": traj[:: max(1, len(traj) // 40)]}
+        print(json.dumps({name: first, "final": out[name]["final"]}), file=sys.stderr, flush=True)
+    return out
+
+
+def run_s_to_tol(args):
+    """--mode s_to_tol: every method of --methods to every tolerance of TOLS
+    (or --tol), each within --budget seconds."""
+    import torch
+    import synth
+
+    r = synth.make_config(args.workload)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    stream = torch.cuda.Stream()
+    tols = sorted({t for t in TOLS if t >= args.tol} | {args.tol}, reverse=True)
+    plan = {m: tols for m in args.methods.split(",")}
+    out = {"mode": "s_to_tol", "workload": workload_name(args, r), "tol": args.tol, "budget_s": args.budget,
+           "methods": s_to_tol_methods(r, x0, plan, args.budget, stream)}
     print(json.dumps(out), flush=True)
+
+
+def run_sweep_once(args):
+    """A short run for profilers: the workload's context with the given launch
+    shapes (--launch; no autotuning), one ALS-NCG iteration (its
+    initialisation includes a sweep), then one sweep timed per kernel class.
+    The sweep kernels launch 3 times in all (2 half sweeps each)."""
+    import torch
+    import synth
+    from paper_1508_03110_gb300 import ALS
+
+    r = synth.make_config(args.workload)
+    x0 = synth.init_factors(r.n_u, r.n_m, r.n_f, 11)
+    stream = torch.cuda.Stream()
+    m = ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, r.n_f, r.lam, precision=args.precision,
+            refine_steps=args.refine, gram_path=args.gram, stream=stream)
+    m.set_x(x0)
+    if args.launch:
+        m.set_launch(**{k: (v if k == "gram_path" and not v.isdigit() else int(v))
+                        for k, v in (kv.split("=") for kv in args.launch.split(","))})
+    m.step(info=False)
+    ts = m.time_sweep(reps=1)
+    m.close()
+    print(json.dumps({"mode": "sweep_once", "workload": workload_name(args, r), "timing": ts}), flush=True)
 
 
 def run_serving(args):
@@ -335,6 +383,34 @@ def run_scale(args):
                       "lambda 0.05, mixed precision, FP32 factors, int32 indices", "results": results}), flush=True)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the sweep
+# kernels' launches from one ncu capture of this command's workload, summed
+# over one sweep's launches of that kernel, with the SHA-256 (first 16 hex
+# digits) of the kernel's sources when it was captured.  A figure is reported
+# only while those sources are unchanged.
+TRAFFIC = {}
+TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh", "internal.cuh"),
+                   "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh", "internal.cuh")}
+
+
+def kernel_source_sha(name):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[name]:
+        with open(os.path.join(ROOT, "paper_1508_03110_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(name, launches):
+    """DRAM bytes per launch of `name` (its captured per-sweep total over its
+    launches), or None if not captured for the current sources."""
+    t = TRAFFIC.get(name)
+    if not t or t[0] != kernel_source_sha(name) or launches < 1:
+        return None
+    return t[1] / launches
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -515,6 +591,9 @@ def main():
     if args.mode == "serving":
         run_serving(args)
         return
+    if args.mode == "sweep_once":
+        run_sweep_once(args)
+        return
     if args.mode == "batched":
         run_batched(args)
         return
@@ -523,7 +602,7 @@ def main():
         return
     import torch
     import synth
-    from paper_1508_03110_gb300 import ALS
+    from paper_1508_03110_gb300 import ALS, probe_alu_peaks
 
     torch.cuda.set_device(local)
     dist = None
@@ -553,11 +632,6 @@ def main():
         tune = m.autotune(reps=2)
     launch = m.get_launch()
     m.run(max(args.warmup, 1), 0.0, check_every=max(args.warmup, 1))
-    # DRAM bytes (read + write) of one sweep's launches from an ncu capture
-    # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; none of
-    # the current sweep kernels (the prefetching variant of k_sweep_tc for rows
-    # of >= 256 ratings included) has been captured, so none is reported
-    traffic = None
 
     # ---- timed region: K ALS-NCG iterations (graph replays) ----
     sampler = ClockSampler(local)
@@ -578,49 +652,73 @@ def main():
     value = job_throughput(r.nnz * args.steps, world, t)
     launches = int(info["kernels"])
 
-    # ---- the dominant kernel: the fused sweep (U half + M half launches) ----
-    reps = 5
-    m.sweep(1)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    m.sweep(reps)
-    s1.record(stream)
-    s1.synchronize()
-    t_sweep = s0.elapsed_time(s1) / 1e3 / reps
+    # ---- the dominant kernel, timed per launch with CUDA events on the stream
+    #      each launch runs on (als_time_sweep), after the timed region ----
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak, fp64_peak = probe_alu_peaks()     # measured on this device
+    ts = m.time_sweep(reps=5)
+    t_sweep = ts["sweep_ms"] / 1e3
     use_tc = args.precision == "mixed" and launch["gram_path"] == 2
+    nf, ld = r.n_f, (r.n_f + 3) // 4 * 4
     fl, gram = sweep_flops(r, r.n_f, args.refine, args.precision, launch.get("dual_max", 0) if use_tc else 0)
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    kernels = {}
+    for name in ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split"):
+        k = ts[name]
+        if k["launches"]:
+            kernels[name] = {"ms_per_sweep": k["ms"], "launches_per_sweep": k["launches"], "rows": k["rows"],
+                             "ratings": k["ratings"], "share_of_sweep": k["ms"] / ts["sweep_ms"]}
     if use_tc:
-        # the dense contraction of the sweep is the Gram build of the rows
-        # solved through their n_f x n_f matrix: n_f (n_f + 1) flop per rating
-        # (symmetric); everything else (light rows' F F^T, Cholesky, solves,
-        # residuals) runs on the FP32 ALU
+        # k_sweep_tc (both variants): the dense contraction is the symmetric
+        # Gram, n_f (n_f + 1) flop per rating of its rows; its Cholesky,
+        # solves and residuals run on the FP32 ALU; its gather reads one FP32
+        # factor row (4 ld bytes) plus 8 bytes of id and value per rating
+        k_ms = ts["k_sweep_tc_pf"]["ms"] + ts["k_sweep_tc"]["ms"]
+        k_ratings = ts["k_sweep_tc_pf"]["ratings"] + ts["k_sweep_tc"]["ratings"]
+        k_rows = ts["k_sweep_tc_pf"]["rows"] + ts["k_sweep_tc"]["rows"]
+        k_launches = ts["k_sweep_tc_pf"]["launches"] + ts["k_sweep_tc"]["launches"]
+        gram_k = float(k_ratings) * nf * (nf + 1)
+        alu_k = float(k_rows) * (nf ** 3 / 3.0 + args.refine * 2 * nf ** 2) + \
+            float(k_ratings) * args.refine * 4 * nf
         peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
-        achieved = gram / t_sweep / 1e12
+        achieved = gram_k / (k_ms / 1e3) / 1e12
         peak_note = f"bf16 dense, {peak_src} (burst)"
-        alu_part = {"achieved": (fl - gram) / t_sweep / 1e12, "peak": fp32_peak,
-                    "frac": (fl - gram) / t_sweep / 1e12 / fp32_peak,
-                    "what": "Cholesky, solves, FP32 residuals, and the light rows' d x d matrices "
-                            "(n_f^3/3 + 2 n_f^2 per row, 4 n_f per rating; light rows n_f d (d+1) + d^3/3 + ...)"}
+        alu_part = {"achieved": alu_k / (k_ms / 1e3) / 1e12, "peak": fp32_peak,
+                    "frac": alu_k / (k_ms / 1e3) / 1e12 / fp32_peak,
+                    "peak_source": "FP32 FMA, measured on this device (als_probe_alu_peaks)",
+                    "what": "k_sweep_tc's Cholesky (n_f^3/3), solves (2 n_f^2 per correction) and FP32 "
+                            "residuals (4 n_f per rating per correction)"}
+        gather = {"achieved_gbs": float(k_ratings) * (4 * ld + 8) / (k_ms / 1e3) / 1e9,
+                  "what": "gathered factor rows + ids/values per rating (mostly L2 hits: the fixed side "
+                          "is 10.7 MB (M) or 55 MB (U))"}
+        kname = "k_sweep_tc (both variants: rows of >= 256 ratings prefetch their factor rows)"
+        per_launch_ms = k_ms / max(1, k_launches)
+        work = {"gram_flop_per_launch": gram_k / max(1, k_launches), "ratings": k_ratings, "rows": k_rows,
+                "launches_per_sweep": k_launches, "ms_per_launch": per_launch_ms}
+        traffic = traffic_for("k_sweep_tc", k_launches)
     else:
-        alu_part = None
+        alu_part, gather = None, None
+        k_ms = ts["k_sweep_fma"]["ms"]
         if args.precision == "fp64":
-            peak = 1.25
-            peak_note = "FP64 nominal 1.25 TFLOP/s (GB300)"
+            peak = fp64_peak
+            peak_note = "FP64 FMA, measured on this device (als_probe_alu_peaks)"
         else:
             peak = fp32_peak
-            peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+            peak_note = "FP32 FMA, measured on this device (als_probe_alu_peaks)"
         unit, bound = "TFLOP/s", "alu"
         achieved = fl / t_sweep / 1e12
+        kname = "k_sweep_fma (fused Gram, Cholesky, solves) and the split rows"
+        work = {"flop_per_sweep": fl}
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per sweep (every launch of both halves), ncu",
-                "kernel": "k_sweep_tc + k_sweep_dual (fused gather, tensor-core Gram or light-row d x d matrix, "
-                          "Cholesky, solves)" if use_tc
-                else "k_sweep_fma (fused Gram, Cholesky, solves)",
-                "peak_source": peak_note, "sweep_ms": t_sweep * 1e3,
-                "what": "one sweep P(x): every launch of both half sweeps (split heavy rows included)"}
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch of the kernel (ncu dram__bytes_read.sum + "
+                                "dram__bytes_write.sum)",
+                "kernel": kname, "peak_source": peak_note, "work": work, "sweep_ms": t_sweep * 1e3,
+                "kernels": kernels, "sms": sms,
+                "measured_alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
+                "what": "the dominant kernel's own launch durations (CUDA events on its stream) over one "
+                        "sweep P(x); sweep_ms is the whole sweep"}
+    if gather:
+        roofline["gather"] = gather
     if alu_part:
         roofline["alu_part"] = alu_part
     m.close()
@@ -658,10 +756,35 @@ def main():
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context build from host COO, x0 upload, K iterations, factor download"}
 
+    # ---- seconds to tolerance from the same x_0 (the metric's headline) ----
+    s2t = None
+    if not args.no_s2t and rank == 0:
+        plan = {"mixed_alsncg": [1e-3, 1e-5, 1e-6], "fp64_alsncg": [1e-3, 1e-5], "fp64_als": [1e-2, 1e-3]}
+        meth = s_to_tol_methods(r, x0, plan, args.s2t_budget, stream)
+
+        def sec(name, tol):
+            hit = meth[name]["reached"].get(f"{tol:g}")
+            return None if hit is None else hit["s"]
+        speed = {}
+        for tol, base in ((1e-3, "fp64_als"), (1e-3, "fp64_alsncg"), (1e-5, "fp64_alsncg")):
+            a, b = sec("mixed_alsncg", tol), sec(base, tol)
+            speed[f"mixed_alsncg_over_{base}@{tol:g}"] = None if (a is None or b is None) else b / a
+        s2t = {"what": "seconds of device work from x_0 (seed 11) to |g_k|/|g_0| <= tol; each context "
+                       "autotuned before its clock starts; FP64 ALS excludes its |g| evaluations",
+               "budget_s_per_method": args.s2t_budget,
+               "methods": {k: {"reached": v["reached"], "final": v["final"]} for k, v in meth.items()},
+               "speedup": speed}
+
     cpu = None
     if not args.no_cpu and rank == 0:
+        import oracle
         est, desc, thr = oracle_sample(r, x0, args.cpu_budget)
-        cpu = {"value": r.nnz / est, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+        nthr = oracle.get_threads()
+        oracle.set_threads(1)
+        est1, desc1, _ = oracle_sample(r, x0, args.cpu_budget)
+        oracle.set_threads(nthr)
+        cpu = {"value": r.nnz / est, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+               "one_thread": {"value": r.nnz / est1, "unit": UNIT, "cores": 1, "sample": desc1}}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -677,7 +800,8 @@ def main():
                           "l2": (f"inputs larger than L2 (ratings stored twice: {r.nnz * 16 / 1e6:.0f} MB; "
                                  f"vectors {(r.n_u + r.n_m) * ((r.n_f + 3) // 4 * 4) * (8 if args.precision == 'fp64' else 4) / 1e6:.0f} MB each)")},
                "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "e2e": e2e,
-               "cpu_baseline": cpu, "final_gnorm_rel": info["gnorm"] / info["gnorm0"], **extra}
+               "cpu_baseline": cpu, "s_to_tol": s2t, "final_gnorm_rel": info["gnorm"] / info["gnorm0"],
+               **extra}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

@@ -13,11 +13,20 @@ from . import _lib
 from ._lib import (ALS_FP64, ALS_MIXED, ALS_LS_BACKTRACK, ALS_LS_EXACT, ALS_DT_F64, ALS_DT_F32,  # noqa: F401
                    ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC, ALSError, IterInfo)
 
-__all__ = ["ALS", "ALSBatch", "ALSGroup", "Server", "ALSError", "load", "info_dict", "make_config"]
+__all__ = ["ALS", "ALSBatch", "ALSGroup", "Server", "ALSError", "load", "info_dict", "make_config",
+           "probe_alu_peaks"]
 
 
 def load():
     return _lib.load()
+
+
+def probe_alu_peaks():
+    """Measured dense FMA peaks of the current device (als_probe_alu_peaks):
+    (FP32 TFLOP/s, FP64 TFLOP/s)."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().als_probe_alu_peaks(ctypes.byref(f32), ctypes.byref(f64)), "als_probe_alu_peaks")
+    return f32.value, f64.value
 
 
 def _torch():
@@ -270,6 +279,16 @@ class ALS:
         _lib.check(self.lib.als_autotune(self.ctx, int(reps), ctypes.byref(r)), "als_autotune")
         out = {k: getattr(r, k) for k, _ in r._fields_ if k != "chosen"}
         out.update({k: getattr(r.chosen, k) for k, _ in r.chosen._fields_})
+        return out
+
+    def time_sweep(self, reps=5):
+        """Per-kernel-class launch times of one sweep (als_time_sweep): dict
+        with sweep_ms and, per class name, ms / launches / rows / ratings."""
+        t = _lib.SweepTiming()
+        _lib.check(self.lib.als_time_sweep(self.ctx, int(reps), ctypes.byref(t)), "als_time_sweep")
+        out = {"sweep_ms": t.sweep_ms}
+        for i, name in enumerate(_lib.SWEEP_CLASSES):
+            out[name] = {"ms": t.ms[i], "launches": t.launches[i], "rows": t.rows[i], "ratings": t.ratings[i]}
         return out
 
     def get_launch(self):

@@ -66,6 +66,15 @@ class ServerConfig(ctypes.Structure):
     ]
 
 
+class SweepTiming(ctypes.Structure):
+    _fields_ = [
+        ("sweep_ms", ctypes.c_double), ("ms", ctypes.c_double * 5), ("rows", ctypes.c_int64 * 5),
+        ("ratings", ctypes.c_int64 * 5), ("launches", ctypes.c_int32 * 5),
+    ]
+
+
+SWEEP_CLASSES = ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split")
+
 # name -> (restype, argtypes); the full list of symbols include/als.h declares
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
@@ -104,6 +113,8 @@ SIGNATURES = {
     "als_group_run": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _dbl, _i32, ctypes.POINTER(IterInfo),
                              ctypes.POINTER(_i32)]),
     "als_selftest_wait_expiry": (_i32, [_vp, _dbl, ctypes.POINTER(_i64)]),
+    "als_time_sweep": (_i32, [_vp, _i32, ctypes.POINTER(SweepTiming)]),
+    "als_probe_alu_peaks": (_i32, [ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "als_sync": (_i32, [_vp]),
     "als_destroy": (None, [_vp]),
     "als_last_error": (ctypes.c_char_p, []),

@@ -44,6 +44,20 @@ struct LsParams {
     int mode;   // als_ls_mode
 };
 
+// Per-kernel-class launch timing of a sweep (als_time_sweep): when a context
+// holds a KTimer, each sweep launch records a CUDA event pair on the stream
+// it is launched on.  Classes: 0 k_sweep_tc prefetching variant, 1 k_sweep_tc,
+// 2 k_sweep_dual, 3 k_sweep_fma, 4 the split heavy rows (all their launches).
+enum { KT_TC_PF = 0, KT_TC = 1, KT_DUAL = 2, KT_FMA = 3, KT_SPLIT = 4, KT_NCLASS = 5 };
+struct KTimer {
+    static constexpr int kMax = 16;          // launches per class between two reads
+    cudaEvent_t ev[KT_NCLASS][kMax][2];
+    int n[KT_NCLASS];
+    int depth;                               // > 0 inside the split part: its own launches
+};
+void kt_begin(struct als_ctx *c, int cls, cudaStream_t st);
+void kt_end(struct als_ctx *c, int cls, cudaStream_t st);
+
 struct DevAlloc {
     void *p;
     size_t bytes;
@@ -125,6 +139,8 @@ struct als_ctx {
     int64_t *segu = nullptr, *segm = nullptr;  // device [n_prob + 1] user / item offsets
     int32_t *rowprob = nullptr;                // device [n_u + n_m] problem of each row
     std::vector<int64_t> h_segu, h_segm;
+
+    KTimer *kt = nullptr;                      // set only inside als_time_sweep
 };
 
 #define RED_MAXB 512

@@ -225,7 +225,10 @@ als_status sweep_launch(als_ctx *c, const SweepArgs &a) {
     // one row group per CTA: the hardware packs as many CTAs per SM as fit
     const int64_t want = (a.nrows + G - 1) / G;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)INT32_MAX));
-    kern<<<grid, 128, smem, a.stream ? a.stream : c->stream>>>(a);
+    cudaStream_t st = a.stream ? a.stream : c->stream;
+    kt_begin(c, KT_FMA, st);
+    kern<<<grid, 128, smem, st>>>(a);
+    kt_end(c, KT_FMA, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }

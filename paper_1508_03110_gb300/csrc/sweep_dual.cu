@@ -294,7 +294,10 @@ als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
     if (raise_smem_limit((const void *)k_sweep_dual, smem) != ALS_OK) return ALS_ECUDA;
     ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_dual, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
-    k_sweep_dual<<<(unsigned)a.nrows, DU_THREADS, smem, a.stream ? a.stream : c->stream>>>(a, nmax);
+    cudaStream_t st = a.stream ? a.stream : c->stream;
+    kt_begin(c, KT_DUAL, st);
+    k_sweep_dual<<<(unsigned)a.nrows, DU_THREADS, smem, st>>>(a, nmax);
+    kt_end(c, KT_DUAL, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }

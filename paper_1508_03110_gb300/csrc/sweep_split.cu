@@ -326,10 +326,23 @@ void count_sweep_rows(als_ctx *c) {
     }
 }
 
+als_status split_sweep_launches(als_ctx *c, const SweepArgs &a, int side, cudaStream_t stream);
+
 als_status launch_split_sweep(als_ctx *c, const SweepArgs &a, int side) {
-    const int64_t H = c->nsplit[side], S = c->nseg[side];
+    const int64_t H = c->nsplit[side];
     if (H == 0) return ALS_OK;
     cudaStream_t stream = a.stream ? a.stream : c->stream;
+    kt_begin(c, KT_SPLIT, stream);
+    if (c->kt) c->kt->depth++;
+    const als_status st = split_sweep_launches(c, a, side, stream);
+    if (c->kt) c->kt->depth--;
+    kt_end(c, KT_SPLIT, stream);
+    return st;
+}
+
+// the launches of launch_split_sweep (timed there as one class)
+als_status split_sweep_launches(als_ctx *c, const SweepArgs &a, int side, cudaStream_t stream) {
+    const int64_t H = c->nsplit[side], S = c->nseg[side];
     // 1. segment partials
     SweepArgs b = a;
     b.nbig = 0;

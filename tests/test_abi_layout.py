@@ -20,6 +20,7 @@ def _structs():
         "als_launch": (_lib.Launch, {}),
         "als_tune_report": (_lib.TuneReport, {}),
         "als_server_config": (_lib.ServerConfig, {}),
+        "als_sweep_timing": (_lib.SweepTiming, {}),
     }
 
 
