@@ -14,7 +14,15 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   ls_coeffs       pinned: Q(alpha) equals loss(x + alpha p) at five alphas,
                   c1 equals grad . p
   backtracking    pinned: Armijo acceptance/rejection invariants of Algorithm 3
-  ncg (Alg. 2)    pinned: equals textbook preconditioned CG on a convex quadratic
+  more_thuente    pinned: the same step as an independent implementation of the
+                  published search (scipy's MINPACK-2 port) on random quartics;
+                  strong Wolfe conditions hold at the step
+  beta_bar        pinned: every form gives preconditioned CG on a convex quadratic
+                  (exact line search), and plain NCG gives textbook CG
+  ncg (Alg. 2)    pinned: equals textbook preconditioned CG on a convex quadratic;
+                  fallback / restart branch: a failed line search reproduces ALS
+                  bit for bit, a non-descent direction takes the preconditioner
+                  point, beta restarts at 0 after every fallback
   als / alsncg    pinned: reach the closed-form global minimum of a fully
                   observed problem; ALS decreases f monotonically
   foldin          pinned: equals the user half-sweep row for a user already in R
@@ -22,6 +30,6 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
 """
 from .core import (  # noqa: F401
     Problem, build_problem, loss, grad, half_sweep, solve_rows, sweep, ls_coeffs, chol_solve,
-    foldin, q_eval, backtracking, exact_step, ncg, als, alsncg, set_threads,
-    get_threads, IterRecord,
+    foldin, q_eval, q_deriv, backtracking, exact_step, more_thuente, beta_bar, BETA_FORMS, ncg, als,
+    alsncg, set_threads, get_threads, IterRecord,
 )

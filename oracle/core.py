@@ -17,6 +17,7 @@ takes):
 """
 import ctypes
 import dataclasses
+import math
 
 import numpy as np
 
@@ -259,8 +260,186 @@ def exact_step(c) -> LineSearchResult:
 
 
 # --------------------------------------------------------------------------
+# Variant: the More-Thuente line search (the paper's serial experiments, §IV,
+# use it: sufficient-decrease tolerance 1e-4, curvature tolerance 1e-2,
+# initial step 1, at most 20 evaluations).  Written from the published
+# algorithm (More & Thuente, ACM TOMS 20(3), 1994): trial steps in an
+# interval of uncertainty, updated by the cases of its Section 4 (cubic,
+# quadratic and secant steps), first on the auxiliary function
+# psi(a) = phi(a) - phi(0) - ftol a phi'(0), then on phi itself; the
+# extrapolation range [1.1, 4] x the last move when nothing is bracketed.
+# phi is Q - c0 (difference form) and phi' = Q', both exact here.
+# --------------------------------------------------------------------------
+
+def q_deriv(c, alpha) -> float:
+    """Q'(alpha) = c1 + 2 c2 alpha + 3 c3 alpha^2 + 4 c4 alpha^3."""
+    return float(c[1] + alpha * (2.0 * c[2] + alpha * (3.0 * c[3] + alpha * 4.0 * c[4])))
+
+
+def _cubic_step(a, fa, da, b, fb, db):
+    """Minimiser of the cubic through (a, fa) and (b, fb) with slopes da, db
+    (Nocedal & Wright, Numerical Optimization, eq. 3.59), or None when that
+    cubic has no real local minimiser."""
+    d1 = da + db - 3.0 * (fa - fb) / (a - b)
+    disc = d1 * d1 - da * db
+    if disc < 0.0:
+        return None
+    d2 = math.copysign(math.sqrt(disc), b - a)
+    den = db - da + 2.0 * d2
+    if den == 0.0:
+        return None
+    return b - (b - a) * (db + d2 - d1) / den
+
+
+def _quad_step(a, fa, da, b, fb):
+    """Minimiser of the quadratic through (a, fa) with slope da and (b, fb)."""
+    return a + 0.5 * da * (b - a) ** 2 / (fa - fb + da * (b - a))
+
+
+def _secant_step(a, da, b, db):
+    """Zero of the line through the slopes (a, da) and (b, db)."""
+    return b - db * (b - a) / (db - da)
+
+
+def _mt_trial(x, fx, dx, y, fy, dy, t, ft, dt, brackt, lo, hi):
+    """One trial-step choice and interval update of More & Thuente (§4).
+    x: the best step so far, y: the other end, t: the current trial.
+    Returns (x, fx, dx, y, fy, dy, t_next, brackt)."""
+    same = dt * math.copysign(1.0, dx) > 0.0
+    if ft > fx:
+        # case 1: a higher value -> the minimiser is bracketed by x and t
+        c = _cubic_step(x, fx, dx, t, ft, dt)
+        q = _quad_step(x, fx, dx, t, ft)
+        if c is None:
+            c = q
+        nxt = c if abs(c - x) < abs(q - x) else c + 0.5 * (q - c)
+        brackt = True
+    elif not same:
+        # case 2: lower value, slopes of opposite sign -> bracketed by x and t
+        c = _cubic_step(x, fx, dx, t, ft, dt)
+        sct = _secant_step(x, dx, t, dt)
+        if c is None:
+            c = sct
+        nxt = c if abs(c - t) >= abs(sct - t) else sct
+        brackt = True
+    elif abs(dt) < abs(dx):
+        # case 3: lower value, same slope sign, slope decreasing in size
+        c = _cubic_step(x, fx, dx, t, ft, dt)
+        beyond = c is not None and (c - t) * (t - x) > 0.0
+        if not beyond:
+            c = hi if t > x else lo
+        sct = _secant_step(x, dx, t, dt)
+        if brackt:
+            nxt = c if abs(c - t) < abs(sct - t) else sct
+            lim = t + 0.66 * (y - t)
+            nxt = min(lim, nxt) if t > x else max(lim, nxt)
+        else:
+            nxt = c if abs(c - t) > abs(sct - t) else sct
+            nxt = min(hi, max(lo, nxt))
+    else:
+        # case 4: lower value, same slope sign, slope not decreasing
+        if brackt:
+            c = _cubic_step(t, ft, dt, y, fy, dy)
+            nxt = c if c is not None else 0.5 * (t + y)
+        else:
+            nxt = hi if t > x else lo
+    # the interval: the end points keep the minimiser between them
+    if ft > fx:
+        y, fy, dy = t, ft, dt
+    else:
+        if not same:
+            y, fy, dy = x, fx, dx
+        x, fx, dx = t, ft, dt
+    return x, fx, dx, y, fy, dy, nxt, brackt
+
+
+def more_thuente(c, alpha0=1.0, ftol=1e-4, gtol=1e-2, xtol=1e-15, stpmin=1e-15, stpmax=1e15,
+                 maxfev=20) -> "LineSearchResult":
+    """The More-Thuente search for a step satisfying the strong Wolfe
+    conditions on Q: Q(a) - Q(0) <= ftol a Q'(0) and |Q'(a)| <= gtol |Q'(0)|.
+    `shrinks` holds the number of evaluations.  If no such step is found
+    within maxfev evaluations (or the interval collapses), the best step seen
+    is taken when it gives sufficient decrease; otherwise the search fails."""
+    g0 = float(c[1])
+    if not (g0 < 0.0):
+        return LineSearchResult(0.0, False, 0, float("inf"))
+    phi = lambda a: a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])))   # noqa: E731  Q(a) - c0
+    gtest = ftol * g0
+    brackt, stage1 = False, True
+    width = stpmax - stpmin
+    width_prev = 2.0 * width
+    x, fx, dx = 0.0, 0.0, g0
+    y, fy, dy = 0.0, 0.0, g0
+    lo, hi = 0.0, alpha0 + 4.0 * alpha0
+    t = min(max(alpha0, stpmin), stpmax)
+    best = None
+    for nfev in range(1, maxfev + 1):
+        ft, dt = phi(t), q_deriv(c, t)
+        ftest = t * gtest
+        if ft <= ftest and (best is None or ft < best[1]):
+            best = (t, ft)
+        if stage1 and ft <= ftest and dt >= 0.0:
+            stage1 = False
+        if ft <= ftest and abs(dt) <= -gtol * g0:
+            return LineSearchResult(t, True, nfev, float("inf"))
+        if (brackt and (t <= lo or t >= hi)) or (brackt and hi - lo <= xtol * hi) or \
+                (t == stpmax and ft <= ftest and dt <= gtest) or (t == stpmin and (ft > ftest or dt >= gtest)):
+            break
+        if stage1 and ft <= fx and ft > ftest:
+            # the auxiliary function psi = phi - a gtest
+            x, fxm, dxm, y, fym, dym, t_new, brackt = _mt_trial(
+                x, fx - x * gtest, dx - gtest, y, fy - y * gtest, dy - gtest, t, ft - t * gtest, dt - gtest,
+                brackt, lo, hi)
+            fx, dx = fxm + x * gtest, dxm + gtest
+            fy, dy = fym + y * gtest, dym + gtest
+        else:
+            x, fx, dx, y, fy, dy, t_new, brackt = _mt_trial(x, fx, dx, y, fy, dy, t, ft, dt, brackt, lo, hi)
+        if brackt:
+            if abs(y - x) >= 0.66 * width_prev:
+                t_new = x + 0.5 * (y - x)
+            width_prev = width
+            width = abs(y - x)
+            lo, hi = min(x, y), max(x, y)
+        else:
+            lo, hi = t_new + 1.1 * (t_new - x), t_new + 4.0 * (t_new - x)
+        t_new = min(max(t_new, stpmin), stpmax)
+        if (brackt and (t_new <= lo or t_new >= hi)) or (brackt and hi - lo <= xtol * hi):
+            t_new = x
+        t = t_new
+    if best is not None:
+        return LineSearchResult(best[0], True, nfev, float("inf"))
+    return LineSearchResult(0.0, False, nfev, float("inf"))
+
+
+# --------------------------------------------------------------------------
 # Algorithm 2 (generic) and the ALS / ALS-NCG drivers
 # --------------------------------------------------------------------------
+
+BETA_FORMS = ("pr", "fr", "hs", "prplus")
+
+
+def beta_bar(form, gbar_new, g_new, g, gbar, p):
+    """beta-bar_{k+1} in the preconditioned forms (g -> gbar where the
+    direction is built, as in Eq. (8)):
+      pr     Eq. (8): gbar_{k+1}^T (g_{k+1} - g_k) / gbar_k^T g_k
+      fr     Fletcher-Reeves: gbar_{k+1}^T g_{k+1} / gbar_k^T g_k
+      hs     Hestenes-Stiefel: gbar_{k+1}^T (g_{k+1} - g_k) / p_k^T (g_{k+1} - g_k)
+      prplus max(0, pr)
+    On a convex quadratic with an exact line search and a linear
+    preconditioner all four equal preconditioned CG's beta.  A zero
+    denominator gives 0."""
+    y = g_new - g
+    if form in ("pr", "prplus"):
+        den = float(gbar @ g)
+        b = float(gbar_new @ y) / den if den != 0.0 else 0.0
+        return max(0.0, b) if form == "prplus" else b
+    if form == "fr":
+        den = float(gbar @ g)
+        return float(gbar_new @ g_new) / den if den != 0.0 else 0.0
+    if form == "hs":
+        den = float(p @ y)
+        return float(gbar_new @ y) / den if den != 0.0 else 0.0
+    raise ValueError(f"unknown beta form {form!r}")
 
 @dataclasses.dataclass
 class IterRecord:
@@ -278,20 +457,26 @@ class IterRecord:
     g: np.ndarray = None
 
 
-def ncg(x0, grad_fn, precond_fn, step_fn, iters, on_iter=None):
+def ncg(x0, grad_fn, precond_fn, step_fn, iters, on_iter=None, beta="pr"):
     """Algorithm 2 with a general preconditioner P and gradient g:
       gbar_0 = x_0 - P(x_0), p_0 = -gbar_0;
       each k: alpha_k from step_fn, x_{k+1} = x_k + alpha_k p_k,
               gbar_{k+1} = x_{k+1} - P(x_{k+1}),
-              beta_{k+1} = gbar_{k+1}^T (g_{k+1} - g_k) / (gbar_k^T g_k)  (Eq. 8),
+              beta_{k+1} = gbar_{k+1}^T (g_{k+1} - g_k) / (gbar_k^T g_k)  (Eq. 8,
+                           or another form of beta_bar()),
               p_{k+1} = -gbar_{k+1} + beta_{k+1} p_k.
     step_fn(x, p, g) -> LineSearchResult.  A failed step takes the
     preconditioner point xbar_k and restarts the direction (beta = 0).
+    precond_fn = None is plain NCG (P = identity in the preconditioned
+    gradient: gbar = g); a failed step then keeps x_k and restarts along -g.
     on_iter(k, x, g, info_dict) is called after every iteration."""
     x = np.array(x0, dtype=np.float64, copy=True)
     g = grad_fn(x)
-    xbar = precond_fn(x)
-    gbar = x - xbar
+    if precond_fn is None:
+        xbar, gbar = x.copy(), g
+    else:
+        xbar = precond_fn(x)
+        gbar = x - xbar
     p = -gbar
     s = float(gbar @ g)
     for k in range(iters):
@@ -300,27 +485,35 @@ def ncg(x0, grad_fn, precond_fn, step_fn, iters, on_iter=None):
             x = x + ls.alpha * p
         else:
             x = xbar.copy()
-        xbar = precond_fn(x)
-        gbar_new = x - xbar
         g_new = grad_fn(x)
-        if ls.ok and s != 0.0:
-            beta = float(gbar_new @ (g_new - g)) / s
+        if precond_fn is None:
+            xbar, gbar_new = x.copy(), g_new
         else:
-            beta = 0.0
-        p = -gbar_new + beta * p
+            xbar = precond_fn(x)
+            gbar_new = x - xbar
+        if ls.ok:
+            b = beta_bar(beta, gbar_new, g_new, g, gbar, p)
+        else:
+            b = 0.0
+        p = -gbar_new + b * p
         s = float(gbar_new @ g_new)
         g, gbar = g_new, gbar_new
+        beta_k = b
         if on_iter is not None:
-            on_iter(k, x, g, dict(alpha=ls.alpha, beta=beta, fallback=not ls.ok,
+            on_iter(k, x, g, dict(alpha=ls.alpha, beta=beta_k, fallback=not ls.ok,
                                   shrinks=ls.shrinks, margin=ls.margin,
                                   state=dict(p=p, gbar=gbar, xbar=xbar, s=s)))
     return x
 
 
 def alsncg(P: Problem, x0, iters, alpha0=10.0, tau=0.9, cc=0.5, max_shrinks=200,
-           mode="backtrack", keep_x=True):
+           mode="backtrack", keep_x=True, beta="pr", precond="als", c2=1e-2):
     """ALS-NCG (Algorithm 2) with P = one ALS sweep and the line search of §V-C.
-    Returns the list of IterRecord, one per iteration (after the update)."""
+    Variants: mode "exact" (minimiser of Q) or "mt" (More-Thuente on Q with
+    sufficient decrease cc, curvature c2, start alpha0 and at most
+    max_shrinks evaluations); beta one of BETA_FORMS; precond "none" is plain
+    NCG (gbar = g).  Returns the list of IterRecord, one per iteration (after
+    the update)."""
     recs = []
     last_c = {}
 
@@ -329,6 +522,8 @@ def alsncg(P: Problem, x0, iters, alpha0=10.0, tau=0.9, cc=0.5, max_shrinks=200,
         last_c["c"] = c
         if mode == "exact":
             return exact_step(c)
+        if mode == "mt":
+            return more_thuente(c, alpha0, cc, c2, maxfev=max_shrinks)
         return backtracking(c, alpha0, tau, cc, max_shrinks)
 
     def on_iter(k, x, g, info):
@@ -338,7 +533,8 @@ def alsncg(P: Problem, x0, iters, alpha0=10.0, tau=0.9, cc=0.5, max_shrinks=200,
                                gnorm=float(np.linalg.norm(g)), c=last_c.get("c"),
                                g=g.copy() if keep_x else None, **info))
 
-    ncg(x0, lambda x: grad(P, x), lambda x: sweep(P, x), step, iters, on_iter)
+    pre = None if precond == "none" else (lambda x: sweep(P, x))
+    ncg(x0, lambda x: grad(P, x), pre, step, iters, on_iter, beta=beta)
     return recs
 
 

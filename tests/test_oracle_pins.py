@@ -237,22 +237,30 @@ def test_exact_step_minimises_quartic():
 
 # -- Algorithm 2 ---------------------------------------------------------------------
 
-def test_ncg_wrapper_reproduces_pcg():
+@pytest.mark.parametrize("beta", ["pr", "fr", "hs", "prplus"])
+@pytest.mark.parametrize("plain", [False, True])
+def test_ncg_wrapper_reproduces_pcg(beta, plain):
     """§III-B: on f = x^T A x / 2 - b^T x with a linear preconditioner
     P(x) = x - B (A x - b) and an exact line search, Algorithm 2 with beta of
-    Eq. (8) is preconditioned CG (textbook form, Nocedal & Wright Alg. 5.3)."""
+    Eq. (8) is preconditioned CG (textbook form, Nocedal & Wright Alg. 5.3).
+    So are the Fletcher-Reeves, Hestenes-Stiefel and PR+ forms of beta-bar
+    (on a quadratic with exact steps they coincide), and plain NCG
+    (gbar = g) is textbook CG (B = I)."""
     n = 12
     rng = np.random.default_rng(5)
     Q = rng.normal(size=(n, n)); A = Q @ Q.T + n * np.eye(n)
     C = rng.normal(size=(n, n)); B = np.linalg.inv(C @ C.T + n * np.eye(n))
+    if plain:
+        B = np.eye(n)
     b = rng.normal(size=n); x0 = rng.normal(size=n)
     iters = []
 
     def step(x, p, g):
         return oracle.core.LineSearchResult(float(-(g @ p) / (p @ A @ p)), True, 0, np.inf)
 
-    oracle.ncg(x0, lambda x: A @ x - b, lambda x: x - B @ (A @ x - b), step, n,
-               on_iter=lambda k, x, g, info: iters.append(x.copy()))
+    pre = None if plain else (lambda x: x - B @ (A @ x - b))
+    oracle.ncg(x0, lambda x: A @ x - b, pre, step, n,
+               on_iter=lambda k, x, g, info: iters.append(x.copy()), beta=beta)
     # textbook PCG
     x = x0.copy(); r = A @ x - b; y = B @ r; p = -y
     ref = []
@@ -472,3 +480,119 @@ def test_fallback_then_resume_restarts_beta():
         p = -gbar + beta * p_prev
         assert np.allclose(r.state["p"], p, rtol=0, atol=1e-12 * np.abs(p).max())
         x_prev, g_prev, gbar_prev, p_prev = r.x, g, gbar, r.state["p"]
+
+
+# -- the More-Thuente line search on Q (variant; the paper's serial runs, §IV) ----------
+
+def _random_quartics(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        scale = 10.0 ** rng.uniform(-3, 3)
+        c = np.array([rng.normal() * scale, -abs(rng.normal()) * scale, rng.normal() * scale,
+                      rng.normal() * scale, (abs(rng.normal()) + 0.01) * scale])
+        out.append(c)
+    return out
+
+
+def test_more_thuente_meets_strong_wolfe():
+    """Every converged step satisfies Q(a) - Q(0) <= ftol a Q'(0) and
+    |Q'(a)| <= gtol |Q'(0)|, with the paper's tolerances."""
+    n_ok = 0
+    for c in _random_quartics(400, 1):
+        ls = oracle.more_thuente(c, 1.0, 1e-4, 1e-2)
+        assert ls.ok
+        a = ls.alpha
+        dq = a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])))
+        assert dq <= 1e-4 * a * c[1] + 1e-12 * abs(c[1]) * a
+        if ls.shrinks < 20:
+            assert abs(oracle.q_deriv(c, a)) <= 1e-2 * abs(c[1]) * (1 + 1e-9)
+            n_ok += 1
+    assert n_ok >= 390
+
+
+def test_more_thuente_equals_an_independent_implementation():
+    """The same published algorithm, implemented independently (scipy's port
+    of MINPACK-2's dcsrch, reached through scalar_search_wolfe1), picks the
+    same step on random quartics wherever both converge."""
+    L = pytest.importorskip("scipy.optimize._linesearch")
+    agree = compared = 0
+    for c in _random_quartics(400, 2):
+        phi = lambda a: a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])))   # noqa: E731
+        dphi = lambda a: oracle.q_deriv(c, a)                               # noqa: E731
+        ref = L.scalar_search_wolfe1(phi, dphi, phi0=0.0, derphi0=float(c[1]), c1=1e-4, c2=1e-2,
+                                     amax=1e15, amin=1e-15, xtol=1e-15)[0]
+        ls = oracle.more_thuente(c, 1.0, 1e-4, 1e-2, maxfev=100)
+        if ref is None or not ls.ok or ls.shrinks >= 100:
+            continue
+        compared += 1
+        if abs(ls.alpha - ref) <= 1e-8 * abs(ref):
+            agree += 1
+    assert compared >= 350
+    assert agree == compared, (agree, compared)
+
+
+def test_more_thuente_on_a_quadratic_takes_the_minimiser():
+    """On Q with c3 = c4 = 0 (a quadratic), once alpha0 = 1 fails the
+    curvature test the cubic/quadratic interpolation is exact, so the search
+    lands on the minimiser -c1 / (2 c2)."""
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        c2 = abs(rng.normal()) + 0.1
+        amin = 10.0 ** rng.uniform(-2, 2)
+        c = np.array([1.0, -2.0 * c2 * amin, c2, 0.0, 0.0])
+        ls = oracle.more_thuente(c, 1.0, 1e-4, 1e-2)
+        assert ls.ok
+        if abs(amin - 1.0) > 0.02 * amin:
+            assert ls.alpha == pytest.approx(amin, rel=1e-10)
+
+
+@pytest.mark.parametrize("beta", ["pr", "fr", "hs", "prplus"])
+def test_beta_forms_on_recomputed_vectors(beta):
+    """Each beta-bar form, per iteration of ALS-NCG, from the vectors
+    recomputed from scratch (sweep, gradient) rather than the loop's own."""
+    P, x0 = _small_problem(n_u=30, n_m=20, n_f=3, seed=21)
+    recs = oracle.alsncg(P, x0, 8, beta=beta)
+    g, gbar = oracle.grad(P, x0), x0 - oracle.sweep(P, x0)
+    p = -gbar
+    for r in recs:
+        gn, gbn = oracle.grad(P, r.x), r.x - oracle.sweep(P, r.x)
+        y = gn - g
+        ref = {"pr": gbn @ y / (gbar @ g), "fr": gbn @ gn / (gbar @ g), "hs": gbn @ y / (p @ y),
+               "prplus": max(0.0, gbn @ y / (gbar @ g))}[beta]
+        if r.fallback:
+            ref = 0.0
+        assert r.beta == pytest.approx(float(ref), rel=1e-9, abs=1e-300)
+        g, gbar, p = gn, gbn, r.state["p"]
+
+
+def test_plain_ncg_restarts_in_place():
+    """Plain NCG (gbar = g): a failed line search keeps x_k and restarts along
+    -g_k; an accepted one moves along p.  f never increases."""
+    P, x0 = _small_problem(n_u=30, n_m=20, n_f=3, seed=22)
+    recs = oracle.alsncg(P, x0, 30, precond="none", max_shrinks=3, alpha0=0.03)
+    assert any(r.fallback for r in recs) and not all(r.fallback for r in recs)
+    x_prev, f_prev = x0, oracle.loss(P, x0)
+    for r in recs:
+        g = oracle.grad(P, r.x)
+        if r.fallback:
+            assert np.array_equal(r.x, x_prev)
+            assert np.array_equal(r.state["p"], -g)
+        assert np.array_equal(r.state["gbar"], g)
+        assert r.f <= f_prev * (1 + 1e-15)
+        x_prev, f_prev = r.x, r.f
+
+
+def test_alsncg_with_more_thuente_reaches_dense_minimum():
+    """ALS-NCG with the More-Thuente search (the paper's serial setting:
+    alpha0 = 1, ftol 1e-4, gtol 1e-2, 20 evaluations) reaches the closed-form
+    global minimum of a fully observed problem."""
+    rng = np.random.default_rng(9)
+    n_u, n_m, n_f, lam = 30, 20, 3, 0.1
+    R = rng.normal(size=(n_u, n_f)) @ rng.normal(size=(n_f, n_m)) + 0.1 * rng.normal(size=(n_u, n_m))
+    rows, cols = np.nonzero(np.ones((n_u, n_m)))
+    P = oracle.build_problem(n_u, n_m, n_f, lam, rows, cols, R[rows, cols])
+    x0 = synth.init_factors(n_u, n_m, n_f, 3)
+    recs = oracle.alsncg(P, x0, 300, alpha0=1.0, cc=1e-4, max_shrinks=20, mode="mt", c2=1e-2)
+    fstar = _dense_minimum(R, n_f, lam)
+    assert recs[-1].f == pytest.approx(fstar, rel=1e-8)
