@@ -9,13 +9,17 @@ order), given the same input factors as the GPU.
 
 Tolerances:
   * FP64 form: 1e-10 relative (per sampled row, per vector, per coefficient);
-  * mixed form, one-pass quantities (gradient, Q coefficients) from the same
-    FP32-representable inputs: 1e-5 relative -- FP32 products and
-    compensated FP32 sums over up to 33k ratings, FP64 totals;
-  * mixed sweep rows: the refinement from the current row u0 leaves an error
-    of at most rho * |u* - u0| with rho = |I - A_bf16^-1 A|, of order
-    kappa(A_i) * 2^-16; from a random start (|u* - u0| ~ |u*|) the bound
-    used is 5e-2 |u* - u0| per row (the same as the small-case test);
+  * mixed form, one-pass quantities from the same FP32-representable inputs
+    (FP32 products, compensated FP32 sums over up to 33k ratings, FP64
+    totals): the gradient within 1e-6 per row, relative to |g_row| + |x_row|
+    (measured 1.1e-7), and each Q coefficient within 1e-6 of its own
+    magnitude (measured: 9e-8 for c1 = g^T p, 3e-8 for c3, below 1e-10 for
+    c0, c2, c4), with c1 equal to the oracle's g^T p;
+  * mixed sweep rows at the default refine_steps: the stopping rule leaves
+    at most 1e-6 of the step |u* - u0| (rho = |I - Ahat^-1 A| per
+    correction), plus the FP32 floor 4 kappa(A_i) 2^-24 |u*| (residual,
+    factor and stored row in FP32), per sampled row (measured: 1e-7 of the
+    step);
   * mixed vs FP64 GPU run: f within 1e-5 relative at equal iteration count.
 """
 import numpy as np
@@ -103,10 +107,29 @@ def test_fullsize_mixed_one_pass_quantities(big):
         c = m.linesearch_coeffs(p)
         f = m.loss()
     gref = oracle.grad(P, xf)
-    assert np.linalg.norm(g - gref) <= 1e-5 * np.linalg.norm(gref)
+    assert np.linalg.norm(g - gref) <= 1e-6 * np.linalg.norm(gref)
+    sc = np.abs(gref).reshape(-1, r.n_f) + np.abs(xf).reshape(-1, r.n_f)
+    assert _row_rel(g.reshape(-1, r.n_f), gref.reshape(-1, r.n_f), scale=sc) < 1e-6
     cref = oracle.ls_coeffs(P, xf, p)
-    assert np.all(np.abs(c - cref) <= 1e-5 * np.abs(cref).max())
+    assert np.all(np.abs(c - cref) <= 1e-6 * np.abs(cref)), (c - cref) / cref
+    assert c[1] == pytest.approx(float(gref @ p), rel=1e-6)      # c1 = g^T p (Armijo slope)
     assert abs(f - oracle.loss(P, xf)) <= 1e-6 * abs(f)
+
+
+def _kappas(ptr, idx, F, lam, rows):
+    out = np.empty(len(rows))
+    for t, i in enumerate(rows):
+        a, b = ptr[i], ptr[i + 1]
+        Fi = F[idx[a:b]]
+        w = np.linalg.eigvalsh(Fi.T @ Fi + lam * (b - a) * np.eye(F.shape[1]))
+        out[t] = w[-1] / max(w[0], 1e-300)
+    return out
+
+
+def _excess(u, ustar, u0, kap, lead=1e-6, C=4.0):
+    err = np.linalg.norm(u - ustar, axis=1)
+    bound = lead * np.linalg.norm(ustar - u0, axis=1) + C * kap * 2.0 ** -24 * np.linalg.norm(ustar, axis=1)
+    return float(np.max(np.where(err == 0.0, 0.0, err / np.maximum(bound, 1e-300))))
 
 
 def test_fullsize_mixed_sweep_sampled_rows(big):
@@ -124,10 +147,10 @@ def test_fullsize_mixed_sweep_sampled_rows(big):
     M1 = x1[r.n_u * nf:].reshape(r.n_m, nf)
     su, sm = _sample(R["uorder"]), _sample(R["morder"])
     ref_u = oracle.solve_rows(P, 0, M0.reshape(-1), su).reshape(-1, nf)
-    assert _row_rel(U1[su], ref_u, scale=ref_u - U0[su]) < 5e-2
+    assert _excess(U1[su], ref_u, U0[su], _kappas(P.uptr, P.uidx, M0, r.lam, su)) < 1.0
     U1f = U1.astype(np.float32).astype(np.float64)
     ref_m = oracle.solve_rows(P, 1, U1f.reshape(-1), sm).reshape(-1, nf)
-    assert _row_rel(M1[sm], ref_m, scale=ref_m - M0[sm]) < 5e-2
+    assert _excess(M1[sm], ref_m, M0[sm], _kappas(P.mptr, P.midx, U1f, r.lam, sm)) < 1.0
 
 
 def test_fullsize_mixed_f_matches_fp64_run(big):

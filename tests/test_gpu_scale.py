@@ -3,8 +3,11 @@
 exact solves of sampled rows -- the heaviest, the lightest and a random set
 -- each from that row's own ratings and the same fixed factors (needs a
 GB300).  Tolerances as in the full-size ML20M-shaped test: FP64 1e-10 per
-row; mixed, from a random start, 5e-2 of the step per row and f within 1e-5
-of the FP64 run at equal iteration count."""
+row; mixed, from a random start, each row within 1e-6 of its step plus the
+FP32 floor 4 kappa(A_i) 2^-24 |u*| (the heaviest item rows, up to 1.2e6
+ratings, are split across CTAs and their partial Gram matrices added in
+FP64; measured: at most 1e-7 of the step), and f within 1e-5 of the FP64 run
+at equal iteration count."""
 import numpy as np
 import pytest
 
@@ -48,6 +51,22 @@ def _row_rel(a, b, scale=None):
     return float(np.max(np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(s, axis=1), 1e-300)))
 
 
+def _kappas(P, side, F, rows):
+    ptr, idx = (P.uptr, P.uidx) if side == 0 else (P.mptr, P.midx)
+    out = np.empty(len(rows))
+    for t, i in enumerate(rows):
+        Fi = F[idx[ptr[i]:ptr[i + 1]]]
+        w = np.linalg.eigvalsh(Fi.T @ Fi + P.lam * (ptr[i + 1] - ptr[i]) * np.eye(F.shape[1]))
+        out[t] = w[-1] / max(w[0], 1e-300)
+    return out
+
+
+def _excess(u, ustar, u0, kap, lead=1e-6, C=4.0):
+    err = np.linalg.norm(u - ustar, axis=1)
+    bound = lead * np.linalg.norm(ustar - u0, axis=1) + C * kap * 2.0 ** -24 * np.linalg.norm(ustar, axis=1)
+    return float(np.max(np.where(err == 0.0, 0.0, err / np.maximum(bound, 1e-300))))
+
+
 @pytest.mark.parametrize("n_f,precision", [(10, "fp64"), (50, "mixed")])
 def test_scale_sweep_sampled_rows(data, n_f, precision):
     from paper_1508_03110_gb300 import ALS
@@ -75,8 +94,8 @@ def test_scale_sweep_sampled_rows(data, n_f, precision):
         assert _row_rel(U1[su], ref_u) < 1e-10
         assert _row_rel(M1[sm], ref_m) < 1e-10
     else:
-        assert _row_rel(U1[su], ref_u, scale=ref_u - U0[su]) < 5e-2
-        assert _row_rel(M1[sm], ref_m, scale=ref_m - M0[sm]) < 5e-2
+        assert _excess(U1[su], ref_u, U0[su], _kappas(Pu, 0, M0, np.arange(len(su)))) < 1.0
+        assert _excess(M1[sm], ref_m, M0[sm], _kappas(Pm, 1, U1x, np.arange(len(sm)))) < 1.0
 
 
 def test_scale_mixed_f_matches_fp64(data):
