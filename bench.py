@@ -388,9 +388,12 @@ def run_scale(args):
 # over one sweep's launches of that kernel, with the SHA-256 (first 16 hex
 # digits) of the kernel's sources when it was captured.  A figure is reported
 # only while those sources are unchanged.
-TRAFFIC = {}
-TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh", "internal.cuh"),
-                   "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh", "internal.cuh")}
+# Captured on a GB300 (profiles/sweep_dram_traffic_ml20m.md): the 4 launches
+# of k_sweep_tc in one sweep read 634.2 MB and wrote 15.4 MB; the 2 launches
+# of k_sweep_dual read 116.4 MB and wrote 35.6 MB.
+TRAFFIC = {"k_sweep_tc": ("aaebd828c8ee6793", 649_568_512), "k_sweep_dual": ("91b1801e7dcbadbf", 152_011_520)}
+TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh"),
+                   "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh")}
 
 
 def kernel_source_sha(name):
@@ -730,6 +733,7 @@ def main():
         m64.set_x(x0)
         m64.sweep(1)
         torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         m64.sweep(1)
         s1.record(stream)
