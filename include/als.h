@@ -77,7 +77,22 @@ typedef enum {
 } als_status;
 
 typedef enum { ALS_FP64 = 0, ALS_MIXED = 1 } als_precision;
-typedef enum { ALS_LS_BACKTRACK = 0, ALS_LS_EXACT = 1 } als_ls_mode;
+/* Line search of Algorithm 2 on Q(alpha): Algorithm 3 backtracking (the
+ * paper's parallel method, §V-C); the exact minimiser of Q among the real
+ * roots of Q'; or the More-Thuente search for a step meeting the strong
+ * Wolfe conditions (the paper's serial experiments, §IV: ls_c = 1e-4,
+ * ls_c2 = 1e-2, ls_alpha0 = 1, at most ls_max_shrinks = 20 evaluations). */
+typedef enum { ALS_LS_BACKTRACK = 0, ALS_LS_EXACT = 1, ALS_LS_MORE_THUENTE = 2 } als_ls_mode;
+/* Form of beta-bar (§III-B): Eq. (8) (Polak-Ribiere with the preconditioned
+ * gradient), Fletcher-Reeves gbar_{k+1}.g_{k+1} / gbar_k.g_k,
+ * Hestenes-Stiefel gbar_{k+1}.(g_{k+1}-g_k) / p_k.(g_{k+1}-g_k), or
+ * max(0, Eq. 8).  On a convex quadratic with exact steps all four give
+ * preconditioned CG. */
+typedef enum { ALS_BETA_PR = 0, ALS_BETA_FR = 1, ALS_BETA_HS = 2, ALS_BETA_PR_PLUS = 3 } als_beta_form;
+/* Preconditioner of Algorithm 2: one ALS sweep (ALS-NCG), or none (plain
+ * NCG, §III-B: gbar = g; a failed line search keeps x_k and restarts the
+ * direction along -g_k). */
+typedef enum { ALS_PRECOND_ALS = 0, ALS_PRECOND_NONE = 1 } als_precond;
 typedef enum { ALS_DT_F64 = 0, ALS_DT_F32 = 1 } als_dtype;
 typedef enum { ALS_GRAM_AUTO = 0, ALS_GRAM_FMA = 1, ALS_GRAM_TC = 2 } als_gram_path;
 
@@ -107,6 +122,9 @@ typedef struct {
     als_alloc_fn alloc;
     als_free_fn free;
     void *alloc_user;
+    int32_t beta_form;        /* als_beta_form (ALS_BETA_PR: Eq. 8)           */
+    int32_t preconditioner;   /* als_precond (ALS_PRECOND_ALS: ALS-NCG)       */
+    double ls_c2;             /* More-Thuente curvature tolerance (1e-2)      */
 } als_config;
 
 /* Per-iteration record of Algorithm 2. */
@@ -129,7 +147,8 @@ typedef struct {
 } als_iter_info;
 
 /* Fill *cfg with the paper's defaults: alpha0 = 10, tau = 0.9, c = 0.5
- * (§V-C), 200 shrinks, backtracking, FP64, one refinement step, auto Gram. */
+ * (§V-C), 200 shrinks, backtracking, FP64, one refinement step, auto Gram,
+ * beta-bar of Eq. (8), the ALS preconditioner, ls_c2 = 1e-2. */
 ALS_API void als_config_default(als_config *cfg);
 
 /* Build a context from ratings (§II, §V-B: R is stored twice, by user and by

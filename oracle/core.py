@@ -293,7 +293,7 @@ def _cubic_step(a, fa, da, b, fb, db):
 
 def _quad_step(a, fa, da, b, fb):
     """Minimiser of the quadratic through (a, fa) with slope da and (b, fb)."""
-    return a + 0.5 * da * (b - a) ** 2 / (fa - fb + da * (b - a))
+    return a + 0.5 * da * ((b - a) * (b - a)) / (fa - fb + da * (b - a))
 
 
 def _secant_step(a, da, b, db):

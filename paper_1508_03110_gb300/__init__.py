@@ -61,17 +61,35 @@ class _Buf:
             self.on_device = 0
 
 
+BETA_FORMS = {"pr": _lib.ALS_BETA_PR, "fr": _lib.ALS_BETA_FR, "hs": _lib.ALS_BETA_HS,
+              "prplus": _lib.ALS_BETA_PR_PLUS}
+# the More-Thuente search with the paper's serial settings (§IV) unless given
+MT_DEFAULTS = dict(ls_alpha0=1.0, ls_c=1e-4, ls_c2=1e-2, ls_max_shrinks=20)
+
+
 def make_config(n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=2, gram_path="auto",
-                hbm_budget_bytes=0, ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
-    """An als_config with the library defaults and the given fields."""
+                hbm_budget_bytes=0, ls_alpha0=None, ls_tau=0.9, ls_c=None, ls_max_shrinks=None,
+                beta="pr", precond="als", ls_c2=None):
+    """An als_config with the library defaults and the given fields.
+    ls_mode: "backtrack" (Algorithm 3), "exact" or "more-thuente"; beta: one
+    of BETA_FORMS; precond: "als" (ALS-NCG) or "none" (plain NCG)."""
     cfg = _lib.Config()
     _lib.load().als_config_default(ctypes.byref(cfg))
     cfg.n_f = int(n_f)
     cfg.lam = float(lam)
     cfg.precision = {"fp64": ALS_FP64, "mixed": ALS_MIXED}[precision]
-    cfg.ls_mode = {"backtrack": ALS_LS_BACKTRACK, "exact": ALS_LS_EXACT}[ls_mode]
-    cfg.ls_alpha0, cfg.ls_tau, cfg.ls_c = float(ls_alpha0), float(ls_tau), float(ls_c)
+    cfg.ls_mode = {"backtrack": ALS_LS_BACKTRACK, "exact": ALS_LS_EXACT,
+                   "more-thuente": _lib.ALS_LS_MORE_THUENTE}[ls_mode]
+    dflt = MT_DEFAULTS if ls_mode == "more-thuente" else dict(ls_alpha0=10.0, ls_c=0.5, ls_c2=1e-2,
+                                                               ls_max_shrinks=200)
+    ls_alpha0 = dflt["ls_alpha0"] if ls_alpha0 is None else ls_alpha0
+    ls_c = dflt["ls_c"] if ls_c is None else ls_c
+    ls_c2 = dflt["ls_c2"] if ls_c2 is None else ls_c2
+    ls_max_shrinks = dflt["ls_max_shrinks"] if ls_max_shrinks is None else ls_max_shrinks
+    cfg.ls_alpha0, cfg.ls_tau, cfg.ls_c, cfg.ls_c2 = float(ls_alpha0), float(ls_tau), float(ls_c), float(ls_c2)
     cfg.ls_max_shrinks = int(ls_max_shrinks)
+    cfg.beta_form = BETA_FORMS[beta]
+    cfg.preconditioner = {"als": _lib.ALS_PRECOND_ALS, "none": _lib.ALS_PRECOND_NONE}[precond]
     cfg.refine_steps = int(refine_steps)
     cfg.gram_path = {"auto": ALS_GRAM_AUTO, "fma": ALS_GRAM_FMA, "tc": ALS_GRAM_TC}[gram_path]
     cfg.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -87,12 +105,13 @@ class ALS:
 
     def __init__(self, n_u, n_m, rows, cols, vals, n_f, lam, precision="fp64", ls_mode="backtrack",
                  refine_steps=2, gram_path="auto", hbm_budget_bytes=0, stream=None, rowptr=None,
-                 ls_alpha0=10.0, ls_tau=0.9, ls_c=0.5, ls_max_shrinks=200):
+                 ls_alpha0=None, ls_tau=0.9, ls_c=None, ls_max_shrinks=None, beta="pr", precond="als",
+                 ls_c2=None):
         torch = _torch()
         self.lib = _lib.load()
         self.n_u, self.n_m, self.n_f = int(n_u), int(n_m), int(n_f)
         cfg = make_config(self.n_f, lam, precision, ls_mode, refine_steps, gram_path, hbm_budget_bytes,
-                          ls_alpha0, ls_tau, ls_c, ls_max_shrinks)
+                          ls_alpha0, ls_tau, ls_c, ls_max_shrinks, beta, precond, ls_c2)
         # device memory comes from torch's caching allocator
         self._blocks = {}
 
@@ -317,7 +336,8 @@ class ALSBatch(ALS):
     problem's M rows."""
 
     def __init__(self, problems, n_f, lam, precision="fp64", ls_mode="backtrack", refine_steps=2,
-                 gram_path="auto", hbm_budget_bytes=0, stream=None):
+                 gram_path="auto", hbm_budget_bytes=0, stream=None, **variant):
+        """variant: make_config's line-search, beta and preconditioner keywords."""
         torch = _torch()
         self.lib = _lib.load()
         self.n_prob = len(problems)
@@ -325,7 +345,8 @@ class ALSBatch(ALS):
         self.n_u = sum(s[0] for s in self.sizes)
         self.n_m = sum(s[1] for s in self.sizes)
         self.n_f = int(n_f)
-        cfg = make_config(self.n_f, lam, precision, ls_mode, refine_steps, gram_path, hbm_budget_bytes)
+        cfg = make_config(self.n_f, lam, precision, ls_mode, refine_steps, gram_path, hbm_budget_bytes,
+                          **variant)
 
         def _alloc(nbytes, stream_, user):
             return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream_ or 0)

@@ -15,7 +15,9 @@ STATUS_NAMES = {0: "ALS_OK", 1: "ALS_EINVAL", 2: "ALS_ENOMEM", 3: "ALS_EBUDGET",
                 5: "ALS_ENOTSPD", 6: "ALS_ELINESEARCH", 7: "ALS_ETIMEOUT", 8: "ALS_EBUSY",
                 9: "ALS_ENOTSUP"}
 ALS_FP64, ALS_MIXED = 0, 1
-ALS_LS_BACKTRACK, ALS_LS_EXACT = 0, 1
+ALS_LS_BACKTRACK, ALS_LS_EXACT, ALS_LS_MORE_THUENTE = 0, 1, 2
+ALS_BETA_PR, ALS_BETA_FR, ALS_BETA_HS, ALS_BETA_PR_PLUS = 0, 1, 2, 3
+ALS_PRECOND_ALS, ALS_PRECOND_NONE = 0, 1
 ALS_DT_F64, ALS_DT_F32 = 0, 1
 ALS_GRAM_AUTO, ALS_GRAM_FMA, ALS_GRAM_TC = 0, 1, 2
 
@@ -30,7 +32,8 @@ class Config(ctypes.Structure):
         ("ls_c", ctypes.c_double), ("ls_max_shrinks", ctypes.c_int32),
         ("refine_steps", ctypes.c_int32), ("gram_path", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("alloc", ALLOC_FN), ("free", FREE_FN),
-        ("alloc_user", ctypes.c_void_p),
+        ("alloc_user", ctypes.c_void_p), ("beta_form", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+        ("ls_c2", ctypes.c_double),
     ]
 
 

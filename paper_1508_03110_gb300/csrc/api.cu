@@ -98,6 +98,8 @@ LsParams ls_params(const als_ctx *c) {
     p.c = c->cfg.ls_c;
     p.max_shrinks = c->cfg.ls_max_shrinks;
     p.mode = c->cfg.ls_mode;
+    p.c2 = c->cfg.ls_c2;
+    p.beta = c->cfg.beta_form;
     return p;
 }
 
@@ -172,8 +174,10 @@ PassArgs pass_args(const als_ctx *c, int side) {
     return a;
 }
 
-// gradient of Eq. (1) at X into Gout; per-row terms |g|^2, gbar.g, gbar.(g-gprev)
-als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev) {
+// gradient of Eq. (1) at X into Gout; per-row terms |g|^2, gbar.g,
+// gbar.(g-gprev) and, with P (the Hestenes-Stiefel form of beta-bar),
+// p.(g-gprev).  Gbar == Gout: gbar is the gradient itself (plain NCG).
+als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev, void *P = nullptr) {
     for (int side = 0; side < 2; ++side) {
         PassArgs a = pass_args(c, side);
         a.Xs = side ? mblk(c, X) : ublk(c, X);
@@ -181,6 +185,7 @@ als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev) {
         a.Gout = side ? mblk(c, Gout) : ublk(c, Gout);
         a.Gbar = Gbar ? (side ? mblk(c, Gbar) : ublk(c, Gbar)) : nullptr;
         a.Gprev = Gprev ? (side ? mblk(c, Gprev) : ublk(c, Gprev)) : nullptr;
+        a.Ps = (P && Gprev) ? (side ? mblk(c, P) : ublk(c, P)) : nullptr;
         const int64_t n = side ? c->n_m : c->n_u;
         const int64_t nh = side ? c->nheavy_m : c->nheavy_u;
         a.row_begin = 0;
@@ -237,11 +242,29 @@ als_status read_scalars(als_ctx *c) {
     return ALS_OK;
 }
 
+bool plain_ncg(const als_ctx *c) { return c->cfg.preconditioner == ALS_PRECOND_NONE; }
+
+// plain NCG: gbar = g (copied from the gradient just formed) and xbar = x
+// (a failed line search keeps x and restarts along -g)
+als_status plain_gbar(als_ctx *c, void *G) {
+    const size_t bytes = (size_t)(c->n_u + c->n_m) * c->ld * c->esz;
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->Gbar, G, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    ALS_CUDA_TRY(cudaMemcpyAsync(c->Xbar, c->X, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return ALS_OK;
+}
+
 als_status ncg_init(als_ctx *c) {
     // gbar_0 = x_0 - P(x_0), g_0 = grad f(x_0), p_0 = -gbar_0, s_0 = gbar_0 . g_0
-    als_status s = sweep_into(c, c->X, c->Xbar, c->Gbar);
-    if (s != ALS_OK) return s;
-    s = grad_into(c, c->X, c->G[c->gcur], c->Gbar, nullptr);
+    als_status s;
+    if (plain_ncg(c)) {
+        s = grad_into(c, c->X, c->G[c->gcur], c->G[c->gcur], nullptr);
+        if (s != ALS_OK) return s;
+        s = plain_gbar(c, c->G[c->gcur]);
+    } else {
+        s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+        if (s != ALS_OK) return s;
+        s = grad_into(c, c->X, c->G[c->gcur], c->Gbar, nullptr);
+    }
     if (s != ALS_OK) return s;
     s = launch_reduce(c, 3, c->n_u + c->n_m, S_RED, POST_INIT, ls_params(c));
     if (s != ALS_OK) return s;
@@ -260,11 +283,18 @@ als_status ncg_iter(als_ctx *c, int gcur) {
     if (s != ALS_OK) return s;
     s = launch_update_x(c);
     if (s != ALS_OK) return s;
-    s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+    const bool hs = c->cfg.beta_form == ALS_BETA_HS;
+    if (plain_ncg(c)) {
+        s = grad_into(c, c->X, c->G[gcur ^ 1], c->G[gcur ^ 1], c->G[gcur], hs ? c->P : nullptr);
+        if (s != ALS_OK) return s;
+        s = plain_gbar(c, c->G[gcur ^ 1]);
+    } else {
+        s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+        if (s != ALS_OK) return s;
+        s = grad_into(c, c->X, c->G[gcur ^ 1], c->Gbar, c->G[gcur], hs ? c->P : nullptr);
+    }
     if (s != ALS_OK) return s;
-    s = grad_into(c, c->X, c->G[gcur ^ 1], c->Gbar, c->G[gcur]);
-    if (s != ALS_OK) return s;
-    s = launch_reduce(c, 3, c->n_u + c->n_m, S_RED, POST_BETA, ls_params(c));
+    s = launch_reduce(c, hs ? 4 : 3, c->n_u + c->n_m, S_RED, POST_BETA, ls_params(c));
     if (s != ALS_OK) return s;
     return launch_update_p(c);
 }
@@ -385,6 +415,9 @@ extern "C" void als_config_default(als_config *cfg) {
     cfg->ls_max_shrinks = 200;
     cfg->refine_steps = 2;
     cfg->gram_path = ALS_GRAM_AUTO;
+    cfg->beta_form = ALS_BETA_PR;
+    cfg->preconditioner = ALS_PRECOND_ALS;
+    cfg->ls_c2 = 1e-2;
 }
 
 namespace {
@@ -446,7 +479,19 @@ static als_status create_impl(const als_config *cfg, int64_t n_u, int64_t n_m, i
     if (cfg->n_f < 1 || cfg->n_f > ALS_MAX_NF) { als_set_error("als_create: n_f must be in 1..128"); return ALS_EINVAL; }
     if (!(cfg->lambda >= 0.0) || !std::isfinite(cfg->lambda)) { als_set_error("als_create: lambda must be finite and >= 0"); return ALS_EINVAL; }
     if (cfg->precision != ALS_FP64 && cfg->precision != ALS_MIXED) { als_set_error("als_create: bad precision"); return ALS_EINVAL; }
-    if (cfg->ls_mode != ALS_LS_BACKTRACK && cfg->ls_mode != ALS_LS_EXACT) { als_set_error("als_create: bad ls_mode"); return ALS_EINVAL; }
+    if (cfg->ls_mode != ALS_LS_BACKTRACK && cfg->ls_mode != ALS_LS_EXACT && cfg->ls_mode != ALS_LS_MORE_THUENTE) {
+        als_set_error("als_create: bad ls_mode");
+        return ALS_EINVAL;
+    }
+    if (cfg->beta_form < ALS_BETA_PR || cfg->beta_form > ALS_BETA_PR_PLUS) { als_set_error("als_create: bad beta_form"); return ALS_EINVAL; }
+    if (cfg->preconditioner != ALS_PRECOND_ALS && cfg->preconditioner != ALS_PRECOND_NONE) {
+        als_set_error("als_create: bad preconditioner");
+        return ALS_EINVAL;
+    }
+    if (cfg->ls_mode == ALS_LS_MORE_THUENTE && !(cfg->ls_c2 > cfg->ls_c && cfg->ls_c2 < 1.0 && cfg->ls_max_shrinks >= 1)) {
+        als_set_error("als_create: the More-Thuente search needs 0 < ls_c < ls_c2 < 1 and ls_max_shrinks >= 1");
+        return ALS_EINVAL;
+    }
     if (!(cfg->ls_alpha0 > 0) || !(cfg->ls_tau > 0 && cfg->ls_tau < 1) || !(cfg->ls_c > 0 && cfg->ls_c < 1) || cfg->ls_max_shrinks < 0) {
         als_set_error("als_create: line-search parameters need alpha0 > 0, 0 < tau < 1, 0 < c < 1");
         return ALS_EINVAL;

@@ -42,6 +42,8 @@ struct LsParams {
     double alpha0, tau, c;
     int max_shrinks;
     int mode;   // als_ls_mode
+    double c2;  // More-Thuente curvature tolerance
+    int beta;   // als_beta_form
 };
 
 // Per-kernel-class launch timing of a sweep (als_time_sweep): when a context

@@ -92,14 +92,20 @@ __device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int6
     T g[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) g[i] = l2 * x[i] - T(2) * acc[i];
-    double tg = 0, tgb = 0, tgd = 0;
+    double tg = 0, tgb = 0, tgd = 0, tpd = 0;
     if (act) {
         st4(reinterpret_cast<T *>(a.Gout) + row * a.ld + 4 * gl, g);
 #pragma unroll
         for (int i = 0; i < 4; ++i) tg += (double)g[i] * (double)g[i];
         if (a.Gbar) {
+            // Gbar == Gout: plain NCG, gbar is this gradient
             T gb[4];
-            ld4(reinterpret_cast<const T *>(a.Gbar) + row * a.ld + 4 * gl, gb);
+            if (a.Gbar == a.Gout) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gb[i] = g[i];
+            } else {
+                ld4(reinterpret_cast<const T *>(a.Gbar) + row * a.ld + 4 * gl, gb);
+            }
             T gp[4];
             if (a.Gprev) ld4(reinterpret_cast<const T *>(a.Gprev) + row * a.ld + 4 * gl, gp);
             else zero4(gp);
@@ -108,16 +114,25 @@ __device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int6
                 tgb += (double)gb[i] * (double)g[i];
                 tgd += (double)gb[i] * ((double)g[i] - (double)gp[i]);
             }
+            if (a.Ps) {
+                // p_k . (g_{k+1} - g_k): the Hestenes-Stiefel denominator
+                T pk[4];
+                ld4(reinterpret_cast<const T *>(a.Ps) + row * a.ld + 4 * gl, pk);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tpd += (double)pk[i] * ((double)g[i] - (double)gp[i]);
+            }
         }
     }
     tg = gsum<LPR>(tg, mask);
     tgb = gsum<LPR>(tgb, mask);
     tgd = gsum<LPR>(tgd, mask);
+    if (a.Ps) tpd = gsum<LPR>(tpd, mask);
     if (gl == 0) {
         const int64_t o = a.rowoff + row;
         a.rowterm[o] = tg;
         a.rowterm[a.stride + o] = tgb;
         a.rowterm[2 * a.stride + o] = tgd;
+        if (a.Ps) a.rowterm[3 * a.stride + o] = tpd;
     }
 }
 
@@ -544,12 +559,159 @@ __device__ int cubic_roots(double a, double b, double c, double d, double *r) {
     return n;
 }
 
+// ---- More-Thuente search on Q (variant; More & Thuente 1994) -------------
+// The same steps as the published algorithm: trial steps in an interval of
+// uncertainty updated by the four cases of its Section 4, first on
+// psi(a) = phi(a) - ftol a phi'(0), then on phi; bisection when the interval
+// fails to shrink by 0.66 over two trials; extrapolation in
+// [1.1, 4] x the last move before anything is bracketed.  phi = Q - c0.
+// Every product and sum is rounded on its own (no contraction).
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ double q_slope(const double *c, double al) {   // Q'(alpha)
+    double t = dmul(dmul(al, 4.0), c[4]);
+    t = dadd(dmul(3.0, c[3]), t);
+    t = dadd(dmul(2.0, c[2]), dmul(al, t));
+    return dadd(c[1], dmul(al, t));
+}
+
+// minimiser of the cubic through (a, fa; slope da) and (b, fb; slope db);
+// false if it has none
+__device__ bool mt_cubic(double a, double fa, double da, double b, double fb, double db, double *out) {
+    const double d1 = dsub(dadd(da, db), ddiv(dmul(3.0, dsub(fa, fb)), dsub(a, b)));
+    const double disc = dsub(dmul(d1, d1), dmul(da, db));
+    if (disc < 0.0) return false;
+    const double d2 = copysign(__dsqrt_rn(disc), dsub(b, a));
+    const double den = dadd(dsub(db, da), dmul(2.0, d2));
+    if (den == 0.0) return false;
+    *out = dsub(b, ddiv(dmul(dsub(b, a), dsub(dadd(db, d2), d1)), den));
+    return true;
+}
+
+__device__ double mt_quad(double a, double fa, double da, double b, double fb) {
+    const double h = dsub(b, a);
+    return dadd(a, ddiv(dmul(dmul(0.5, da), dmul(h, h)), dadd(dsub(fa, fb), dmul(da, h))));
+}
+
+__device__ double mt_secant(double a, double da, double b, double db) {
+    return dsub(b, ddiv(dmul(db, dsub(b, a)), dsub(db, da)));
+}
+
+struct MtEnds {
+    double x, fx, dx, y, fy, dy;
+};
+
+// one trial-step choice and interval update; returns the next trial
+__device__ double mt_trial(MtEnds &e, double t, double ft, double dt, bool &brackt, double lo, double hi) {
+    const bool same = dmul(dt, copysign(1.0, e.dx)) > 0.0;
+    double nxt, cc;
+    if (ft > e.fx) {                                   // case 1
+        const double q = mt_quad(e.x, e.fx, e.dx, t, ft);
+        if (!mt_cubic(e.x, e.fx, e.dx, t, ft, dt, &cc)) cc = q;
+        nxt = fabs(dsub(cc, e.x)) < fabs(dsub(q, e.x)) ? cc : dadd(cc, dmul(0.5, dsub(q, cc)));
+        brackt = true;
+    } else if (!same) {                                // case 2
+        const double sc = mt_secant(e.x, e.dx, t, dt);
+        if (!mt_cubic(e.x, e.fx, e.dx, t, ft, dt, &cc)) cc = sc;
+        nxt = fabs(dsub(cc, t)) >= fabs(dsub(sc, t)) ? cc : sc;
+        brackt = true;
+    } else if (fabs(dt) < fabs(e.dx)) {                // case 3
+        const bool have = mt_cubic(e.x, e.fx, e.dx, t, ft, dt, &cc);
+        const bool beyond = have && dmul(dsub(cc, t), dsub(t, e.x)) > 0.0;
+        if (!beyond) cc = t > e.x ? hi : lo;
+        const double sc = mt_secant(e.x, e.dx, t, dt);
+        if (brackt) {
+            nxt = fabs(dsub(cc, t)) < fabs(dsub(sc, t)) ? cc : sc;
+            const double lim = dadd(t, dmul(0.66, dsub(e.y, t)));
+            nxt = t > e.x ? fmin(lim, nxt) : fmax(lim, nxt);
+        } else {
+            nxt = fabs(dsub(cc, t)) > fabs(dsub(sc, t)) ? cc : sc;
+            nxt = fmin(hi, fmax(lo, nxt));
+        }
+    } else {                                           // case 4
+        if (brackt) {
+            if (!mt_cubic(t, ft, dt, e.y, e.fy, e.dy, &nxt)) nxt = dmul(0.5, dadd(t, e.y));
+        } else {
+            nxt = t > e.x ? hi : lo;
+        }
+    }
+    if (ft > e.fx) {
+        e.y = t; e.fy = ft; e.dy = dt;
+    } else {
+        if (!same) { e.y = e.x; e.fy = e.fx; e.dy = e.dx; }
+        e.x = t; e.fx = ft; e.dx = dt;
+    }
+    return nxt;
+}
+
+// returns ok; *alpha the step, *dq = Q(alpha) - Q(0), *nfev the evaluations
+__device__ bool more_thuente(const double *c, const LsParams &lp, double *alpha, double *dq, int *nfev) {
+    const double g0 = c[1];
+    const double ftol = lp.c, gtol = lp.c2, xtol = 1e-15, stpmin = 1e-15, stpmax = 1e15;
+    const double gtest = dmul(ftol, g0);
+    bool brackt = false, stage1 = true;
+    double width = dsub(stpmax, stpmin), width_prev = dmul(2.0, width);
+    MtEnds e{0.0, 0.0, g0, 0.0, 0.0, g0};
+    double lo = 0.0, hi = dadd(lp.alpha0, dmul(4.0, lp.alpha0));
+    double t = fmin(fmax(lp.alpha0, stpmin), stpmax);
+    bool have_best = false;
+    double best_t = 0.0, best_f = 0.0;
+    int n = 0;
+    while (n < lp.max_shrinks) {
+        ++n;
+        const double ft = q_delta(c, t), dt = q_slope(c, t);
+        const double ftest = dmul(t, gtest);
+        if (ft <= ftest && (!have_best || ft < best_f)) { have_best = true; best_t = t; best_f = ft; }
+        if (stage1 && ft <= ftest && dt >= 0.0) stage1 = false;
+        if (ft <= ftest && fabs(dt) <= dmul(-gtol, g0)) {
+            *alpha = t; *dq = ft; *nfev = n;
+            return true;
+        }
+        if ((brackt && (t <= lo || t >= hi)) || (brackt && dsub(hi, lo) <= dmul(xtol, hi)) ||
+            (t == stpmax && ft <= ftest && dt <= gtest) || (t == stpmin && (ft > ftest || dt >= gtest)))
+            break;
+        double tn;
+        if (stage1 && ft <= e.fx && ft > ftest) {
+            // the auxiliary function psi = phi - a gtest
+            MtEnds m{e.x, dsub(e.fx, dmul(e.x, gtest)), dsub(e.dx, gtest),
+                     e.y, dsub(e.fy, dmul(e.y, gtest)), dsub(e.dy, gtest)};
+            tn = mt_trial(m, t, dsub(ft, dmul(t, gtest)), dsub(dt, gtest), brackt, lo, hi);
+            e.x = m.x; e.fx = dadd(m.fx, dmul(m.x, gtest)); e.dx = dadd(m.dx, gtest);
+            e.y = m.y; e.fy = dadd(m.fy, dmul(m.y, gtest)); e.dy = dadd(m.dy, gtest);
+        } else {
+            tn = mt_trial(e, t, ft, dt, brackt, lo, hi);
+        }
+        if (brackt) {
+            if (fabs(dsub(e.y, e.x)) >= dmul(0.66, width_prev)) tn = dadd(e.x, dmul(0.5, dsub(e.y, e.x)));
+            width_prev = width;
+            width = fabs(dsub(e.y, e.x));
+            lo = fmin(e.x, e.y);
+            hi = fmax(e.x, e.y);
+        } else {
+            lo = dadd(tn, dmul(1.1, dsub(tn, e.x)));
+            hi = dadd(tn, dmul(4.0, dsub(tn, e.x)));
+        }
+        tn = fmin(fmax(tn, stpmin), stpmax);
+        if ((brackt && (tn <= lo || tn >= hi)) || (brackt && dsub(hi, lo) <= dmul(xtol, hi))) tn = e.x;
+        t = tn;
+    }
+    *nfev = n;
+    if (have_best) {   // no strong-Wolfe step: the best step with sufficient decrease
+        *alpha = best_t; *dq = best_f;
+        return true;
+    }
+    return false;
+}
+
 __device__ void post_lselect(double *S, const LsParams lp) {
     const double *c = S + S_C;
     double alpha = 0.0, dq = 0.0;
     int ok = 0, k = 0;
     if (c[1] < 0.0) {
-        if (lp.mode == ALS_LS_EXACT) {
+        if (lp.mode == ALS_LS_MORE_THUENTE) {
+            ok = more_thuente(c, lp, &alpha, &dq, &k) ? 1 : 0;
+        } else if (lp.mode == ALS_LS_EXACT) {
             double r[3];
             const int n = cubic_roots(4.0 * c[4], 3.0 * c[3], 2.0 * c[2], c[1], r);
             double best = 0.0;
@@ -591,7 +753,19 @@ __device__ void run_post(double *S, int s_off, int post, const LsParams &lp) {
     } else if (post == POST_BETA) {
         const double gg = S[s_off], gbg = S[s_off + 1], gbd = S[s_off + 2];
         const double sk = S[S_S];
-        S[S_BETA] = (S[S_MODE] == 0.0 && sk != 0.0) ? gbd / sk : 0.0;
+        double beta = 0.0;
+        if (S[S_MODE] == 0.0) {   // after a fallback the direction restarts
+            if (lp.beta == ALS_BETA_FR) {
+                beta = sk != 0.0 ? gbg / sk : 0.0;
+            } else if (lp.beta == ALS_BETA_HS) {
+                const double pd = S[s_off + 3];
+                beta = pd != 0.0 ? gbd / pd : 0.0;
+            } else {
+                beta = sk != 0.0 ? gbd / sk : 0.0;
+                if (lp.beta == ALS_BETA_PR_PLUS) beta = fmax(0.0, beta);
+            }
+        }
+        S[S_BETA] = beta;
         S[S_S] = gbg;
         S[S_GG] = gg;
     } else if (post == POST_INIT) {
