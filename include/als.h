@@ -185,6 +185,13 @@ ALS_API als_status als_create_batched(const als_config *cfg, int32_t n_prob, con
  * out[q] for q < n_prob (n_prob = 1 for an ordinary context).  Synchronous. */
 ALS_API als_status als_batch_info(als_ctx *ctx, int32_t n_prob, als_iter_info *out);
 
+/* |grad f| of each problem of a batched context at its current factors
+ * (gnorm[q], q < n_prob; n_prob = 1 for an ordinary context), reduced in
+ * FP64 per problem -- the stopping test of plain ALS (Algorithm 1), which
+ * does not form the gradient itself.  Does not change x or the ALS-NCG
+ * state.  Synchronous. */
+ALS_API als_status als_batch_grad_norms(als_ctx *ctx, int32_t n_prob, double *gnorm);
+
 /* Inspection of what the device builder made (§V-B storage), copied to host
  * arrays; any pointer may be NULL.  uptr[n_u+1] / uidx[nnz] / uval[nnz]: by
  * user, items ascending; mptr[n_m+1] / midx[nnz] / mval[nnz]: by item, users
@@ -425,6 +432,28 @@ ALS_API als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter, do
  * ALS_ENOTSUP unless the context uses the tensor-core Gram.  Note that
  * n_u x limit_s / (4 x SMs) seconds pass: use a small problem. */
 ALS_API als_status als_selftest_wait_expiry(als_ctx *ctx, double limit_s, int64_t *expired);
+
+/* Ranking accuracy of the top-t recommendations (§IV, the modified
+ * Kendall-tau metric of the serial experiments).  A user's ranking lists all
+ * items by descending predicted rating u_i . m_j at the context's current
+ * factors (FP64 or FP32 as the context stores them), ties by ascending item
+ * id.  1 <= t <= min(64, n_m); not for batched contexts (ALS_ENOTSUP).
+ *
+ * als_rank_topt: top[i * t + k] = the k-th item of user i's ranking
+ * (n_u x t int32, on_device: device or host memory).  Synchronous for a host
+ * buffer.
+ *
+ * als_rank_accuracy: given reference lists top_ref (n_u x t, e.g. from
+ * als_rank_topt at a converged solution; ids in range and distinct per user,
+ * else ALS_EINVAL), the swaps s_i that bring the reference items one after
+ * the other, in their reference order, to the front of the current ranking
+ * (the k-th move costs the items still ahead of it that are not among the
+ * earlier reference items), q_i = 1 - s_i / s_max, s_max = t (2 n_m - t - 1)
+ * / 2; *q_mean = the mean of q_i over the users (fixed-order FP64 sum);
+ * q_user (nullable, host) receives the n_u values q_i.  Synchronous. */
+ALS_API als_status als_rank_topt(als_ctx *ctx, int32_t t, int32_t *top, int on_device);
+ALS_API als_status als_rank_accuracy(als_ctx *ctx, int32_t t, const int32_t *top_ref, int on_device,
+                                     double *q_mean, double *q_user);
 
 /* Per-kernel timing of one sweep P(x) (no counterpart in the paper: the
  * measurement behind the roofline figures).  Runs `reps` sweeps (1..1000)

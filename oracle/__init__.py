@@ -27,9 +27,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
                   observed problem; ALS decreases f monotonically
   foldin          pinned: equals the user half-sweep row for a user already in R
   solve_rows      pinned: equals the selected rows of half_sweep
+  ranking.*       pinned: the paper's worked example of the top-t metric
+                  (s = 4, q = 5/9), identical and reversed rankings (q = 1, 0),
+                  literal adjacent-swap counting on random permutations
 """
 from .core import (  # noqa: F401
     Problem, build_problem, loss, grad, half_sweep, solve_rows, sweep, ls_coeffs, chol_solve,
     foldin, q_eval, q_deriv, backtracking, exact_step, more_thuente, beta_bar, BETA_FORMS, ncg, als,
     alsncg, set_threads, get_threads, IterRecord,
 )
+from . import ranking  # noqa: F401,E402

@@ -300,6 +300,23 @@ class ALS:
         out.update({k: getattr(r.chosen, k) for k, _ in r.chosen._fields_})
         return out
 
+    def rank_topt(self, t):
+        """The first t items of every user's ranking by the current factors
+        (als_rank_topt): int32 array n_u x t."""
+        out = np.empty((self.n_u, int(t)), np.int32)
+        _lib.check(self.lib.als_rank_topt(self.ctx, int(t), out.ctypes.data, 0), "als_rank_topt")
+        return out
+
+    def rank_accuracy(self, top_ref, per_user=False):
+        """Mean top-t ranking accuracy q against reference lists (n_u x t)
+        (als_rank_accuracy); with per_user also the n_u values q_i."""
+        ref = np.ascontiguousarray(top_ref, np.int32)
+        qm = ctypes.c_double()
+        qu = np.empty(self.n_u, np.float64) if per_user else None
+        _lib.check(self.lib.als_rank_accuracy(self.ctx, int(ref.shape[1]), ref.ctypes.data, 0, ctypes.byref(qm),
+                                              qu.ctypes.data if per_user else None), "als_rank_accuracy")
+        return (qm.value, qu) if per_user else qm.value
+
     def time_sweep(self, reps=5):
         """Per-kernel-class launch times of one sweep (als_time_sweep): dict
         with sweep_ms and, per class name, ms / launches / rows / ratings."""
@@ -397,6 +414,12 @@ class ALSBatch(ALS):
         arr = (IterInfo * self.n_prob)()
         _lib.check(self.lib.als_batch_info(self.ctx, self.n_prob, arr), "als_batch_info")
         return [info_dict(a) for a in arr]
+
+    def grad_norms(self):
+        """|grad f| of every problem at the current factors (als_batch_grad_norms)."""
+        out = (ctypes.c_double * self.n_prob)()
+        _lib.check(self.lib.als_batch_grad_norms(self.ctx, self.n_prob, out), "als_batch_grad_norms")
+        return np.array(out[:])
 
 
 class Server:

@@ -87,6 +87,7 @@ SIGNATURES = {
     "als_create_batched": (_i32, [ctypes.POINTER(Config), _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp,
                                   ctypes.POINTER(_vp)]),
     "als_batch_info": (_i32, [_vp, _i32, ctypes.POINTER(IterInfo)]),
+    "als_batch_grad_norms": (_i32, [_vp, _i32, ctypes.POINTER(_dbl)]),
     "als_get_ratings": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "als_set_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "als_get_factors": (_i32, [_vp, _vp, _vp, _i32, _i32]),
@@ -116,6 +117,8 @@ SIGNATURES = {
     "als_group_run": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _dbl, _i32, ctypes.POINTER(IterInfo),
                              ctypes.POINTER(_i32)]),
     "als_selftest_wait_expiry": (_i32, [_vp, _dbl, ctypes.POINTER(_i64)]),
+    "als_rank_topt": (_i32, [_vp, _i32, _vp, _i32]),
+    "als_rank_accuracy": (_i32, [_vp, _i32, _vp, _i32, ctypes.POINTER(_dbl), _vp]),
     "als_time_sweep": (_i32, [_vp, _i32, ctypes.POINTER(SweepTiming)]),
     "als_probe_alu_peaks": (_i32, [ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "als_sync": (_i32, [_vp]),

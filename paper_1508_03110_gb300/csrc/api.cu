@@ -981,6 +981,22 @@ extern "C" als_status als_batch_info(als_ctx *c, int32_t n_prob, als_iter_info *
     return ALS_OK;
 }
 
+extern "C" als_status als_batch_grad_norms(als_ctx *c, int32_t n_prob, double *gnorm) {
+    if (!c || !gnorm || n_prob != c->n_prob) {
+        als_set_error("als_batch_grad_norms: bad argument (n_prob must equal the context's problem count)");
+        return ALS_EINVAL;
+    }
+    // G[gcur ^ 1] is free between ALS-NCG iterations (the next one overwrites it)
+    als_status s = grad_into(c, c->X, c->G[c->gcur ^ 1], nullptr, nullptr);
+    if (s != ALS_OK) return s;
+    s = launch_reduce(c, 1, c->n_u + c->n_m, S_RED, POST_NONE, ls_params(c));
+    if (s != ALS_OK) return s;
+    s = read_scalars(c);
+    if (s != ALS_OK) return s;
+    for (int q = 0; q < n_prob; ++q) gnorm[q] = std::sqrt(c->hS[(size_t)q * S_COUNT + S_RED]);
+    return ALS_OK;
+}
+
 extern "C" als_status als_sync(als_ctx *c) {
     if (!c) { als_set_error("als_sync: ctx is NULL"); return ALS_EINVAL; }
     ALS_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -286,3 +286,26 @@ def foldin_requests(n_req, n_m, d_min, d_max, seed, item_s=1.0):
     ptr = np.zeros(n_req + 1, np.int64)
     np.cumsum(deg, out=ptr[1:])
     return ptr, cols.astype(np.int32), vals.astype(np.float32)
+
+
+# Serial-experiment shapes (the paper's Tables 1-4 ran on MovieLens-20M
+# subsets of median users and median movies; these synthetic stand-ins have
+# the same shapes, a uniform 5% density and rank-10 half-star values)
+TABLE_SHAPES = ((400, 80), (800, 160), (1600, 320), (3200, 640))
+TABLE_DENSITY = 0.05
+
+
+def table_problem(n_u, n_m, seed, density=TABLE_DENSITY, rank=10):
+    """Each (user, item) pair is rated with probability `density`; a user or
+    item left without ratings gets one at a uniform random partner.  Values:
+    rank-`rank` truth plus N(0, 0.5^2) noise, mean 3.5, half stars.  Returns
+    (rows, cols, vals)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mask = rng.random((n_u, n_m)) < density
+    for i in np.nonzero(~mask.any(axis=1))[0]:
+        mask[i, rng.integers(n_m)] = True
+    for j in np.nonzero(~mask.any(axis=0))[0]:
+        mask[rng.integers(n_u), j] = True
+    rows, cols = np.nonzero(mask)
+    vals = half_star_values(rows, cols, n_u, n_m, rank, rng)
+    return rows.astype(np.int32), cols.astype(np.int32), vals

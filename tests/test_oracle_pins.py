@@ -596,3 +596,73 @@ def test_alsncg_with_more_thuente_reaches_dense_minimum():
     recs = oracle.alsncg(P, x0, 300, alpha0=1.0, cc=1e-4, max_shrinks=20, mode="mt", c2=1e-2)
     fstar = _dense_minimum(R, n_f, lam)
     assert recs[-1].f == pytest.approx(fstar, rel=1e-8)
+
+
+# -- top-t ranking accuracy (§IV) -------------------------------------------------------
+
+def test_ranking_metric_worked_example():
+    """The paper's worked example (tests/golden/kendall_tau_example.json):
+    p1 = [6,3,1,2,4,5], p2 = [3,4,2,5,6,1], t = 2 take 4 swaps (movie 6 from
+    the 5th place to the 1st, movie 3 already 2nd), s_max = 9, q = 5/9."""
+    import json
+    import os
+    from fractions import Fraction
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "kendall_tau_example.json")))
+    s = oracle.ranking.swaps_to_front(g["p1"][:g["t"]], g["p2"])
+    assert s == g["swaps"]
+    assert oracle.ranking.s_max(g["n_m"], g["t"]) == g["s_max"]
+    assert Fraction(1) - Fraction(s, int(oracle.ranking.s_max(g["n_m"], g["t"]))) == Fraction(g["q"])
+
+
+def _adjacent_swaps(top, p2):
+    """Literal count: bubble each reference item forward one adjacent swap at a time."""
+    cur = list(p2)
+    n = 0
+    for k, a in enumerate(top):
+        i = cur.index(a)
+        while i > k:
+            cur[i - 1], cur[i] = cur[i], cur[i - 1]
+            i -= 1
+            n += 1
+    return n, cur
+
+
+def test_ranking_swaps_equal_adjacent_swap_counting():
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        n_m = int(rng.integers(2, 40))
+        t = int(rng.integers(1, n_m + 1))
+        p1, p2 = rng.permutation(n_m), rng.permutation(n_m)
+        n, cur = _adjacent_swaps(list(p1[:t]), list(p2))
+        assert oracle.ranking.swaps_to_front(p1[:t], p2) == n
+        assert list(cur[:t]) == list(p1[:t])
+
+
+def test_ranking_identical_and_reversed():
+    """q = 1 when p2 equals p1 on the top t; s = s_max when p2 is p1 reversed."""
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        n_m = int(rng.integers(2, 60))
+        t = int(rng.integers(1, n_m + 1))
+        p1 = rng.permutation(n_m)
+        assert oracle.ranking.swaps_to_front(p1[:t], p1) == 0
+        assert oracle.ranking.swaps_to_front(p1[:t], p1[::-1]) == oracle.ranking.s_max(n_m, t)
+
+
+def test_rank_accuracy_of_factors():
+    """From factors: the ranking is by descending u . m (ties by id), the
+    reference top-t of the same factors gives q = 1, and q_i equals the
+    paper's procedure applied to the two orderings."""
+    rng = np.random.default_rng(2)
+    U, M = rng.normal(size=(30, 4)), rng.normal(size=(50, 4))
+    top = oracle.ranking.topt(U, M, 5)
+    for i in range(30):
+        assert list(top[i]) == list(np.argsort(-(M @ U[i]), kind="stable")[:5])
+    qm, q, s = oracle.ranking.rank_accuracy(U, M, top)
+    assert qm == 1.0 and np.all(s == 0)
+    U2 = U + 0.3 * rng.normal(size=U.shape)
+    qm2, q2, s2 = oracle.ranking.rank_accuracy(U2, M, top)
+    for i in range(30):
+        n, _ = _adjacent_swaps(list(top[i]), list(np.argsort(-(M @ U2[i]), kind="stable")))
+        assert s2[i] == n
+    assert 0.0 <= qm2 < 1.0
