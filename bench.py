@@ -401,10 +401,9 @@ def run_serving(args):
     arrivals at each rate for `duration` seconds, request degree log-uniform in
     [1, 5000] with Zipf items and half-star values, while `jobs` ALS-NCG
     factorisation jobs (n_f = 20, ratings log-uniform in [1e5, 5e6]) are
-    admitted and run in between.  Latency is submit-to-result on the host."""
-    import random
-    import threading
-
+    admitted and run in between.  Arrivals come from the library's native
+    open-loop generator (als_server_replay); a request's latency runs from
+    its scheduled arrival to its result on the host."""
     import torch
     import synth
     from paper_1508_03110_gb300 import ALS, Server
@@ -429,43 +428,28 @@ def run_serving(args):
         torch.cuda.synchronize()
         for rate in rates:
             n_req = max(1, int(rate * args.duration))
-            rng = random.Random(int(rate))
+            rng = np.random.default_rng(int(rate))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+            sel = np.arange(n_req) % pool_n
+            lens = np.array([len(pool[q][0]) for q in sel], np.int64)
+            rptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+            ritems = np.concatenate([pool[q][0] for q in sel]).astype(np.int32)
+            rvals = np.concatenate([pool[q][1] for q in sel]).astype(np.float32)
             srv = Server(model, max_batch=256, slots=4, max_jobs=2)
-            tickets = []
-            lat = []
-            stop = threading.Event()
-
-            def collector():
-                i = 0
-                while i < n_req:
-                    if i < len(tickets):
-                        lat.append(srv.wait(tickets[i], timeout=120.0)[1])
-                        i += 1
-                    elif stop.is_set():
-                        break
-                    else:
-                        time.sleep(1e-4)
-            th = threading.Thread(target=collector)
-            th.start()
             jt = [srv.submit_job(j[0], j[1], j[2], j[3], j[4], synth.init_factors(j[0], j[1], 20, 9 + q), 20,
                                  20, lam, precision=prec) for q, j in enumerate(jobs)]
+            # arrivals from the native load generator (open loop, Poisson)
             t0 = time.perf_counter()
-            t_next = t0
-            for q in range(n_req):
-                t_next += rng.expovariate(rate)
-                while time.perf_counter() < t_next:
-                    pass
-                tickets.append(srv.submit_foldin(*pool[q % pool_n]))
+            tickets, lag = srv.replay(arrivals, rptr, ritems, rvals)
             t_sub = time.perf_counter() - t0
-            th.join()
+            lat = [srv.wait(int(t), timeout=120.0)[1] for t in tickets]
             t_all = time.perf_counter() - t0
-            stop.set()
             job_lat = [srv.wait(t, timeout=600.0)[1] for t in jt]
             st = srv.stats()
             srv.close()
             lat_ms = np.sort(np.array(lat)) * 1e3
             res = {"precision": prec, "rate_offered": rate, "requests": n_req,
-                   "rate_submitted": n_req / t_sub, "rate_served": n_req / t_all,
+                   "rate_submitted": n_req / t_sub, "max_submit_lag_ms": lag * 1e3, "rate_served": n_req / t_all,
                    "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                    "max_ms": float(lat_ms[-1]), "server_p50_ms": st["p50_s"] * 1e3,
                    "server_p99_ms": st["p99_s"] * 1e3, "job_latency_s": job_lat}

@@ -303,7 +303,9 @@ ALS_API als_status als_foldin(als_ctx *ctx, int64_t n_req, const int64_t *req_pt
  * hbm_budget_bytes and fewer than max_jobs run; each runs on its own context
  * and stream, one iteration at a time, interleaved with the fold-in batches.
  * Every result is computed exactly as it would be alone: rows and jobs are
- * independent, so batching changes timing only.  While a server exists the
+ * independent, so batching changes timing only.  A batch orders its
+ * requests by degree as a sweep orders rows (mixed form: the lightest through
+ * the light-row solve, the heaviest through the prefetching kernel).  While a server exists the
  * model context must not be used by other calls.  All server calls are
  * thread-safe.
  * ------------------------------------------------------------------------- */
@@ -326,6 +328,17 @@ ALS_API als_status als_server_create(als_ctx *model, const als_server_config *cf
  * vals[n]); copies the arrays.  *ticket identifies it. */
 ALS_API als_status als_server_submit_foldin(als_server *srv, int64_t n, const int32_t *items,
                                             const float *vals, int64_t *ticket);
+
+/* Open-loop load generator in native code: submits n_req fold-in requests,
+ * request q (items/vals[req_ptr[q] .. req_ptr[q+1]), host arrays) at
+ * t_arrival[q] seconds after the call starts (non-decreasing), spinning on a
+ * steady clock between arrivals, and returns once all are submitted;
+ * tickets[n_req] receives their tickets.  A request's latency counts from its
+ * scheduled arrival; *max_lag_s (nullable) = the largest delay of a
+ * submission behind its schedule. */
+ALS_API als_status als_server_replay(als_server *srv, int64_t n_req, const double *t_arrival,
+                                     const int64_t *req_ptr, const int32_t *items, const float *vals,
+                                     int64_t *tickets, double *max_lag_s);
 
 /* Enqueue a factorisation job: COO ratings (host), x0 = n_u + n_m rows of
  * cfg->n_f doubles (host), run `iters` ALS-NCG iterations.  Copies inputs.

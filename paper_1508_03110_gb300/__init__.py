@@ -474,6 +474,23 @@ class Server:
         self._kind[t.value] = ("foldin", (self.model.n_f,), np.float32)
         return t.value
 
+    def replay(self, t_arrival, req_ptr, items, vals):
+        """Native open-loop load generator (als_server_replay): submit request q
+        at t_arrival[q] seconds; returns (tickets, largest lag behind schedule)."""
+        t_arrival = np.ascontiguousarray(t_arrival, np.float64)
+        req_ptr = np.ascontiguousarray(req_ptr, np.int64)
+        items = np.ascontiguousarray(items, np.int32)
+        vals = np.ascontiguousarray(vals, np.float32)
+        n = t_arrival.shape[0]
+        tickets = np.empty(n, np.int64)
+        lag = ctypes.c_double()
+        _lib.check(self.lib.als_server_replay(self.srv, n, t_arrival.ctypes.data, req_ptr.ctypes.data,
+                                              items.ctypes.data, vals.ctypes.data, tickets.ctypes.data,
+                                              ctypes.byref(lag)), "als_server_replay")
+        for t in tickets:
+            self._kind[int(t)] = ("foldin", (self.model.n_f,), np.float32)
+        return tickets, lag.value
+
     def submit_job(self, n_u, n_m, rows, cols, vals, x0, iters, n_f, lam, **config):
         """x0: (n_u + n_m) x n_f float64 initial factors; config: make_config's keywords."""
         cfg = make_config(n_f, lam, **config)

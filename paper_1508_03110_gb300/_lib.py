@@ -105,6 +105,7 @@ SIGNATURES = {
     "als_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
     "als_server_create": (_i32, [_vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "als_server_submit_foldin": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
+    "als_server_replay": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)]),
     "als_server_submit_job": (_i32, [_vp, ctypes.POINTER(Config), _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i32,
                                      ctypes.POINTER(_i64)]),
     "als_server_wait": (_i32, [_vp, _i64, _dbl, _vp, ctypes.POINTER(_dbl)]),

@@ -919,8 +919,11 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     int32_t *didx = nullptr;
     float *dval = nullptr;
     void *dout = nullptr;
+    int32_t *dord = nullptr;
     als_status s;
-    auto cleanup = [&]() { ctx_free(c, dptr); ctx_free(c, didx); ctx_free(c, dval); ctx_free(c, dout); };
+    auto cleanup = [&]() {
+        ctx_free(c, dptr); ctx_free(c, didx); ctx_free(c, dval); ctx_free(c, dout); ctx_free(c, dord);
+    };
     if ((s = ctx_alloc(c, (void **)&dptr, (n_req + 1) * sizeof(int64_t))) != ALS_OK) { cleanup(); return s; }
     if ((s = ctx_alloc(c, (void **)&didx, std::max<int64_t>(total, 1) * sizeof(int32_t))) != ALS_OK) { cleanup(); return s; }
     if ((s = ctx_alloc(c, (void **)&dval, std::max<int64_t>(total, 1) * sizeof(float))) != ALS_OK) { cleanup(); return s; }
@@ -942,12 +945,35 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
         als_set_error("als_foldin: item id out of range, non-finite rating or decreasing req_ptr");
         return ALS_EINVAL;
     }
+    // requests by descending degree (ties by position), as a sweep orders its
+    // rows: the heaviest take the prefetching tensor-core kernel, the lightest
+    // (mixed form, lambda > 0) the light-row solve
+    std::vector<int64_t> hp(n_req + 1);
+    TRY(cudaMemcpyAsync(hp.data(), dptr, (n_req + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> hord(n_req);
+    for (int64_t q = 0; q < n_req; ++q) hord[q] = (int32_t)q;
+    std::stable_sort(hord.begin(), hord.end(),
+                     [&](int32_t x, int32_t y) { return hp[x + 1] - hp[x] > hp[y + 1] - hp[y]; });
+    const int T = std::min(c->dual_max, c->nf);
+    const bool dual = c->use_tc && !c->f64 && c->cfg.lambda > 0.0 && T > 0;
+    int64_t npf = 0, ndual = 0;
+    for (int64_t q = 0; q < n_req; ++q) {
+        const int64_t d = hp[hord[q] + 1] - hp[hord[q]];
+        if (d >= ALS_TC_PF_MIN) ++npf;
+        if (dual && d <= T) ++ndual;
+    }
+    if ((s = ctx_alloc(c, (void **)&dord, n_req * sizeof(int32_t))) != ALS_OK) { cleanup(); return s; }
+    TRY(cudaMemcpyAsync(dord, hord.data(), n_req * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     SweepArgs a;
     a.ptr = dptr;
     a.idx = didx;
     a.val = dval;
-    a.order = nullptr;
+    a.order = dord;
     a.nrows = n_req;
+    a.npf = npf;
+    a.ndual = ndual;
+    a.dual_nmax = dual ? T : 0;
     a.F = mblk(c, c->X);
     a.Xin = nullptr;
     a.Xout = dout;

@@ -61,6 +61,7 @@ struct Slot {
     int32_t *hidx = nullptr, *didx = nullptr;
     float *hval = nullptr, *dval = nullptr;
     void *hout = nullptr, *dout = nullptr;
+    int32_t *horder = nullptr, *dorder = nullptr;  // the batch's requests by descending degree
     cudaEvent_t ev = nullptr;
     std::vector<Request *> reqs;
     bool busy = false;
@@ -148,12 +149,32 @@ bool launch_batch(als_server *s, Slot &sl) {
         cudaMemcpyAsync(sl.didx, sl.hidx, nrat * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream);
         cudaMemcpyAsync(sl.dval, sl.hval, nrat * sizeof(float), cudaMemcpyHostToDevice, s->stream);
     }
+    // requests by descending degree (ties by arrival), as the sweep orders
+    // rows: the heaviest take the prefetching tensor-core kernel, the
+    // lightest (at most min(dual_max, n_f) ratings, lambda > 0, mixed form)
+    // the light-row solve through their n_i x n_i matrix
+    int64_t npf = 0, ndual = 0;
+    const int T = std::min(c->dual_max, c->nf);
+    const bool dual = c->use_tc && !c->f64 && c->cfg.lambda > 0.0 && T > 0;
+    for (int64_t q = 0; q < nreq; ++q) sl.horder[q] = (int32_t)q;
+    std::stable_sort(sl.horder, sl.horder + nreq, [&](int32_t x, int32_t y) {
+        return sl.hptr[x + 1] - sl.hptr[x] > sl.hptr[y + 1] - sl.hptr[y];
+    });
+    for (int64_t q = 0; q < nreq; ++q) {
+        const int64_t d = sl.hptr[sl.horder[q] + 1] - sl.hptr[sl.horder[q]];
+        if (d >= ALS_TC_PF_MIN) ++npf;
+        if (dual && d <= T) ++ndual;
+    }
+    cudaMemcpyAsync(sl.dorder, sl.horder, nreq * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream);
     SweepArgs a;
     a.ptr = sl.dptr;
     a.idx = sl.didx;
     a.val = sl.dval;
-    a.order = nullptr;
+    a.order = sl.dorder;
     a.nrows = nreq;
+    a.npf = npf;
+    a.ndual = ndual;
+    a.dual_nmax = dual ? T : 0;
     a.F = (const char *)c->X + (size_t)c->n_u * c->ld * c->esz;
     a.Xin = nullptr;
     a.Xout = sl.dout;
@@ -367,7 +388,9 @@ extern "C" als_status als_server_create(als_ctx *model, const als_server_config 
         if (cudaMallocHost(&sl.hflag, 2 * sizeof(int)) != cudaSuccess || cudaMallocHost(&sl.hptr, (cfg.max_batch + 1) * sizeof(int64_t)) != cudaSuccess ||
             cudaMallocHost(&sl.hidx, cfg.max_batch_ratings * sizeof(int32_t)) != cudaSuccess ||
             cudaMallocHost(&sl.hval, cfg.max_batch_ratings * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost(&sl.hout, ob) != cudaSuccess || cudaMalloc(&sl.dptr, (cfg.max_batch + 1) * sizeof(int64_t)) != cudaSuccess ||
+            cudaMallocHost(&sl.hout, ob) != cudaSuccess || cudaMallocHost(&sl.horder, cfg.max_batch * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&sl.dorder, cfg.max_batch * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&sl.dptr, (cfg.max_batch + 1) * sizeof(int64_t)) != cudaSuccess ||
             cudaMalloc(&sl.didx, cfg.max_batch_ratings * sizeof(int32_t)) != cudaSuccess ||
             cudaMalloc(&sl.dval, cfg.max_batch_ratings * sizeof(float)) != cudaSuccess || cudaMalloc(&sl.dout, ob) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -384,9 +407,57 @@ extern "C" als_status als_server_create(als_ctx *model, const als_server_config 
     return ALS_OK;
 }
 
+namespace {
+// enqueue one fold-in request whose arrival time is t0
+als_status submit_foldin_at(als_server *s, int64_t n, const int32_t *items, const float *vals, int64_t *ticket,
+                            clk::time_point t0);
+}  // namespace
+
 extern "C" als_status als_server_submit_foldin(als_server *s, int64_t n, const int32_t *items, const float *vals,
                                                int64_t *ticket) {
     if (!s || n < 0 || (n > 0 && (!items || !vals)) || !ticket) {
+        als_set_error("als_server_submit_foldin: bad argument");
+        return ALS_EINVAL;
+    }
+    return submit_foldin_at(s, n, items, vals, ticket, clk::now());
+}
+
+extern "C" als_status als_server_replay(als_server *s, int64_t n_req, const double *t_arrival,
+                                        const int64_t *req_ptr, const int32_t *items, const float *vals,
+                                        int64_t *tickets, double *max_lag_s) {
+    if (!s || n_req < 0 || (n_req > 0 && (!t_arrival || !req_ptr || !tickets))) {
+        als_set_error("als_server_replay: bad argument");
+        return ALS_EINVAL;
+    }
+    for (int64_t q = 0; q < n_req; ++q) {
+        if (!(t_arrival[q] >= 0.0) || (q > 0 && t_arrival[q] < t_arrival[q - 1]) || req_ptr[q + 1] < req_ptr[q] ||
+            req_ptr[0] != 0) {
+            als_set_error("als_server_replay: arrival times must be >= 0 and non-decreasing, req_ptr non-decreasing from 0");
+            return ALS_EINVAL;
+        }
+    }
+    const clk::time_point start = clk::now();
+    double lag = 0.0;
+    for (int64_t q = 0; q < n_req; ++q) {
+        const clk::time_point due = start + std::chrono::duration_cast<clk::duration>(
+                                                std::chrono::duration<double>(t_arrival[q]));
+        clk::time_point now = clk::now();
+        while (now < due) now = clk::now();   // open loop: arrivals do not wait for answers
+        lag = std::max(lag, std::chrono::duration<double>(now - due).count());
+        const int64_t b = req_ptr[q], n = req_ptr[q + 1] - b;
+        // latency counts from the scheduled arrival, even when the generator runs late
+        const als_status st = submit_foldin_at(s, n, items ? items + b : nullptr, vals ? vals + b : nullptr,
+                                               tickets + q, due);
+        if (st != ALS_OK) return st;
+    }
+    if (max_lag_s) *max_lag_s = lag;
+    return ALS_OK;
+}
+
+namespace {
+als_status submit_foldin_at(als_server *s, int64_t n, const int32_t *items, const float *vals, int64_t *ticket,
+                            clk::time_point t0) {
+    if (n < 0 || (n > 0 && (!items || !vals))) {
         als_set_error("als_server_submit_foldin: bad argument");
         return ALS_EINVAL;
     }
@@ -406,7 +477,7 @@ extern "C" als_status als_server_submit_foldin(als_server *s, int64_t n, const i
     {
         std::lock_guard<std::mutex> lk(s->mu);
         r->ticket = s->next_ticket++;
-        r->t0 = clk::now();
+        r->t0 = t0;
         if (!s->have_first) {
             s->t_first = r->t0;
             s->have_first = true;
@@ -418,6 +489,7 @@ extern "C" als_status als_server_submit_foldin(als_server *s, int64_t n, const i
     s->cv.notify_one();
     return ALS_OK;
 }
+}  // namespace
 
 extern "C" als_status als_server_submit_job(als_server *s, const als_config *cfg, int64_t n_u, int64_t n_m, int64_t nnz,
                                             const int32_t *rows, const int32_t *cols, const float *vals, const double *x0,
@@ -525,7 +597,8 @@ extern "C" void als_server_destroy(als_server *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (Slot &sl : s->slots) {
         cudaFreeHost(sl.hflag); cudaFreeHost(sl.hptr); cudaFreeHost(sl.hidx); cudaFreeHost(sl.hval); cudaFreeHost(sl.hout);
-        cudaFree(sl.dptr); cudaFree(sl.didx); cudaFree(sl.dval); cudaFree(sl.dout);
+        cudaFreeHost(sl.horder);
+        cudaFree(sl.dptr); cudaFree(sl.didx); cudaFree(sl.dval); cudaFree(sl.dout); cudaFree(sl.dorder);
         if (sl.ev) cudaEventDestroy(sl.ev);
     }
     for (auto &kv : s->reqs) delete kv.second;

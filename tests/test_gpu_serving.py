@@ -159,3 +159,24 @@ def test_server_rejects_bad_requests_and_times_out(tiny):
             srv.wait(t, timeout=0.0)          # just submitted: not finished
         x, _ = srv.wait(t, timeout=120.0)     # the ticket stays valid after a timeout
         assert np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("n_f,precision", [(10, "fp64"), (100, "mixed")])
+def test_replayed_load_equals_direct(tiny, n_f, precision):
+    """Requests offered by the native open-loop generator (Poisson arrivals at
+    2e4 req/s, degrees 1-600, light and heavy rows mixed in every batch) give
+    the same answers as als_foldin on the same model, bit for bit."""
+    from paper_1508_03110_gb300 import Server
+    reqs = _requests(2000, tiny.n_m, seed=24)
+    ptr = np.concatenate([[0], np.cumsum([len(i) for i, _ in reqs])]).astype(np.int64)
+    items = np.concatenate([i for i, _ in reqs]).astype(np.int32)
+    vals = np.concatenate([v for _, v in reqs]).astype(np.float32)
+    arrivals = np.cumsum(np.random.default_rng(5).exponential(1.0 / 2e4, size=len(reqs)))
+    with _model(tiny, n_f, precision) as m:
+        direct = m.foldin(ptr, items, vals, dtype="float32")
+        with Server(m, max_batch=128, slots=4) as srv:
+            tickets, lag = srv.replay(arrivals, ptr, items, vals)
+            got = np.stack([srv.wait(int(t))[0] for t in tickets])
+            st = srv.stats()
+    assert np.array_equal(got, direct)
+    assert st["completed"] == len(reqs) and lag >= 0.0
