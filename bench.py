@@ -496,6 +496,15 @@ def run_batched(args):
             b.run(steps, 0.0, check_every=steps)
             b.sync()
         t_seq = time.perf_counter() - t0
+    # the group again with equal stream priorities
+    with ALSGroup(probs, n_fs, 0.05, precision="mixed", priorities=False) as g:
+        g.set_x(xs)
+        g.run(args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.run(steps, check_every=steps)
+        torch.cuda.synchronize()
+        t_flat = time.perf_counter() - t0
     with ALSGroup(probs, n_fs, 0.05, precision="mixed") as g:
         g.set_x(xs)
         torch.cuda.synchronize()
@@ -506,6 +515,7 @@ def run_batched(args):
     out.update({"ratings": nnz, "iterations": steps, "ms_per_iter_group": t_group / steps * 1e3,
                 "ratings_iter_per_s_group": nnz * steps / t_group,
                 "ms_per_iter_sequential": t_seq / steps * 1e3,
+                "ms_per_iter_group_equal_priorities": t_flat / steps * 1e3,
                 "kernels_per_iter": info["kernels"] / steps,
                 "s_to_1e-4": t_tol, "iters_to_1e-4": conv["iters"], "worst_rel_gnorm": worst})
     print(json.dumps(out), flush=True)
@@ -553,9 +563,21 @@ def run_scale(args):
             e1.record(stream)
             e1.synchronize()
             t_sw = e0.elapsed_time(e1) / 1e3
+            # the sweep against HBM: its algorithmic bytes are, per rating, one
+            # gathered factor row (4 ld) and its id and value (8), and per row
+            # x_in, x_out and gbar (3 x 4 ld), over both halves
+            ld = (nf + 3) // 4 * 4
+            sweep_bytes = 2 * nnz * (4 * ld + 8) + 3 * (n_u + n_m) * 4 * ld
+            ts = m.time_sweep(reps=2)
+            peaks, peak_src = load_peaks()
             res = {"step": step, "n_u": n_u, "n_m": n_m, "ratings": nnz, "target": target, "n_f": nf,
                    "generate_s": gen_s, "build_s": build_s, "ms_per_iter": t_it * 1e3,
                    "ratings_iter_per_s": nnz / t_it, "sweep_ms": t_sw * 1e3, "ratings_per_s_per_sweep": nnz / t_sw,
+                   "sweep_algorithmic_gb": sweep_bytes / 1e9,
+                   "sweep_gbs": sweep_bytes / (ts["sweep_ms"] / 1e3) / 1e9,
+                   "sweep_hbm_frac": sweep_bytes / (ts["sweep_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                   "hbm_peak_source": f"{peak_src} copy bandwidth",
+                   "sweep_kernels_ms": {k: v["ms"] for k, v in ts.items() if isinstance(v, dict) and v["launches"]},
                    "gnorm_rel_after_12": info["gnorm"] / info["gnorm0"],
                    "peak_torch_gb": torch.cuda.max_memory_allocated() / 1e9,
                    "launch": {k: tune[k] for k in ("heavy_min", "grid_mult", "split_min", "seg_len", "gram_path",

@@ -388,6 +388,9 @@ ALS_API void als_server_destroy(als_server *srv);
  *                  n_i x n_i matrix F F^T + lambda n_i I (Woodbury identity:
  *                  the same solution of Eq. (4), from a factorisation of
  *                  n_i^3 / 3 flops instead of n_f^3 / 3); 0..64, 0 = none
+ *   gather_tma     tensor-core sweep, rows of >= 256 ratings: their factor rows
+ *                  are gathered two chunks ahead by TMA (tile::gather4, 1)
+ *                  or one chunk ahead by cp.async (0)
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t heavy_min;        /* default 512    */
@@ -397,6 +400,7 @@ typedef struct {
     int32_t seg_len;          /* default 4096, >= 32 */
     int32_t gram_path;        /* in use         */
     int32_t dual_max;         /* default 64     */
+    int32_t gather_tma;       /* default 0      */
 } als_launch;
 
 ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);

@@ -534,14 +534,26 @@ class ALSGroup:
     problems: list of (n_u, n_m, rows, cols, vals) with local ids; n_fs: the
     n_f of each problem."""
 
-    def __init__(self, problems, n_fs, lam, precision="mixed", autotune=True, **kw):
+    def __init__(self, problems, n_fs, lam, precision="mixed", autotune=True, priorities=True, **kw):
+        """priorities: the member with the most work per iteration (ratings x
+        n_f^2) gets the highest stream priority, the next one the next, so the
+        dominant context's CTAs are dispatched first and the others fill the
+        SMs it leaves idle."""
         torch = _torch()
         self.lib = _lib.load()
         self.order = {}
         for q, nf in enumerate(n_fs):
             self.order.setdefault(int(nf), []).append(q)
         self.n_prob = len(problems)
-        self.streams = {nf: torch.cuda.Stream() for nf in self.order}
+        work = {nf: sum(len(problems[q][4]) for q in qs) * nf * nf for nf, qs in self.order.items()}
+        ranked = sorted(self.order, key=lambda nf: -work[nf])
+        if priorities:
+            least, greatest = torch.cuda.Stream.priority_range()
+            span = list(range(greatest, least + 1)) if greatest <= least else list(range(greatest, least - 1, -1))
+            prio = {nf: span[min(i, len(span) - 1)] for i, nf in enumerate(ranked)}
+        else:
+            prio = {nf: 0 for nf in ranked}
+        self.streams = {nf: torch.cuda.Stream(priority=prio[nf]) for nf in self.order}
         self.batches = {nf: ALSBatch([problems[q] for q in qs], nf, lam, precision=precision,
                                      stream=self.streams[nf], **kw)
                         for nf, qs in self.order.items()}

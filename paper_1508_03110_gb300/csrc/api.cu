@@ -117,6 +117,7 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.order = side ? c->morder : c->uorder;
     a.nrows = side ? c->n_m : c->n_u;
     a.F = F;
+    a.nF = side ? c->n_u : c->n_m;
     a.Xin = Xin;
     a.Xout = Xout;
     a.Gbar = Gbar;
@@ -975,6 +976,7 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     a.ndual = ndual;
     a.dual_nmax = dual ? T : 0;
     a.F = mblk(c, c->X);
+    a.nF = c->n_m;
     a.Xin = nullptr;
     a.Xout = dout;
     a.Gbar = nullptr;
@@ -1105,6 +1107,7 @@ void fill_launch(const als_ctx *c, als_launch *o) {
     o->seg_len = c->seg_len;
     o->gram_path = c->f64 ? ALS_GRAM_FMA : (c->use_tc ? ALS_GRAM_TC : ALS_GRAM_FMA);
     o->dual_max = c->dual_max;
+    o->gather_tma = c->gather_tma;
 }
 
 // apply launch shapes (validated by the caller); rebuilds what depends on them
@@ -1127,6 +1130,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
         if ((s = build_split(c)) != ALS_OK) return s;
     }
     c->dual_max = l.dual_max;
+    c->gather_tma = l.gather_tma;
     count_sweep_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
@@ -1134,7 +1138,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
 
 bool launch_valid(const als_ctx *c, const als_launch &l) {
     if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
-        l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX)
+        l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX || l.gather_tma < 0 || l.gather_tma > 1)
         return false;
     if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
     if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
@@ -1152,7 +1156,8 @@ extern "C" als_status als_get_launch(als_ctx *c, als_launch *out) {
 extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
     if (!c || !in || !launch_valid(c, *in)) {
         als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
-                      "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64)");
+                      "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64, "
+                      "gather_tma 0 or 1)");
         return ALS_EINVAL;
     }
     return apply_launch(c, *in);
@@ -1223,6 +1228,14 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
             als_launch cand = cur;
             cand.split_min = sc[0];
             cand.seg_len = sc[1];
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+    }
+    if (!c->f64 && cur.gram_path == ALS_GRAM_TC) {
+        // the heavy rows' gather: cp.async by the lanes, or TMA gather4
+        for (int g : {0, 1}) {
+            als_launch cand = cur;
+            cand.gather_tma = g;
             if ((s = trial(cand, false, best)) != ALS_OK) return s;
         }
     }
@@ -1331,6 +1344,7 @@ extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64
     a.order = c->uorder;
     a.nrows = c->n_u;
     a.F = mblk(c, c->X);
+    a.nF = c->n_m;
     a.Xin = ublk(c, c->X);
     a.Xout = c->tmpvec;   // scratch: the factors are not touched
     a.Gbar = nullptr;

@@ -114,6 +114,8 @@ struct als_ctx {
     int grid_mult = 32;                // pass grids: at most grid_mult x sm_count CTAs
     int sweep_bin_min = 0;             // FMA sweep, n_f <= 32: rows with >= this many ratings use a CTA (0: none)
     int64_t sweep_big[2] = {0, 0};     // ... their count per side (a prefix of the degree order)
+    int gather_tma = 0;                // tensor-core sweep: heavy rows' factor rows gathered by TMA (1)
+                                       // or by cp.async (0)
     int dual_max = ALS_DUAL_MAX;       // mixed tensor-core sweep: rows of <= min(dual_max, n_f) ratings
                                        // are solved through their n_i x n_i matrix (0: none)
     int64_t sweep_dual[2] = {0, 0};    // ... their count per side (a suffix of the degree order)
@@ -200,6 +202,7 @@ struct SweepArgs {
     const int32_t *order;   // rows to process, in this order (nullptr = 0..nrows-1)
     int64_t nrows;
     const void *F;          // fixed-side factors, ld-strided (T)
+    int64_t nF = 0;         // rows of F (0: unknown; the TMA-fed kernel then is not used)
     const void *Xin;        // current rows (warm start; Gbar = Xin - Xout); may be null
     void *Xout;             // solved rows
     void *Gbar;             // optional Gbar rows

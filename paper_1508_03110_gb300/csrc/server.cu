@@ -176,6 +176,7 @@ bool launch_batch(als_server *s, Slot &sl) {
     a.ndual = ndual;
     a.dual_nmax = dual ? T : 0;
     a.F = (const char *)c->X + (size_t)c->n_u * c->ld * c->esz;
+    a.nF = c->n_m;
     a.Xin = nullptr;
     a.Xout = sl.dout;
     a.Gbar = nullptr;

@@ -34,6 +34,12 @@
 // while the current chunk is split, stored and multiplied, so the gather's L2
 // latency is paid once per row rather than once per chunk.  The staging tile
 // costs 12.8 KB of shared memory (n_f = 100), i.e. 4 CTAs per SM instead of 5.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "internal.cuh"
 #include "sweep_common.cuh"
 #include "tc_ptx.cuh"
@@ -49,12 +55,25 @@ constexpr uint32_t LBO = 1024;  // byte distance between the two 64-wide MN atom
 constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
 constexpr int TMEM_COLS = 128;
 
+// Variants of the gather (template PFM): 0 each lane loads its factor rows
+// from global memory; 1 (prefetching) the next chunk's rows are copied into a
+// staging tile with cp.async by the lanes that will read them; 2 (TMA) the
+// rows of the chunk after next are gathered into one of two staging tiles by
+// tile::gather4 TMA copies, issued by 8 lanes of warp 0, four rows each, and
+// counted on the stage's mbarrier.
+constexpr int NSTG = 1;   // TMA staging tiles (gathers run NSTG chunks ahead)
+
+// bytes between two groups of four gathered rows in a TMA staging tile
+// (each group's destination must be 128-byte aligned)
+__host__ __device__ inline int tma_group_bytes(int ld) { return (4 * ld * 4 + 127) & ~127; }
+
 struct TcLayout {
     int ring, A, vec, mbar, holder, stg, total;
 };
 
-// stg_ld > 0: a staging tile of KCH factor rows of stg_ld floats (PF variant)
-__host__ __device__ inline TcLayout tc_layout(int nf, int stg_ld = 0) {
+// mode 1: a staging tile of KCH factor rows of ld floats; mode 2: NSTG TMA
+// staging tiles of KCH / 4 row groups
+__host__ __device__ inline TcLayout tc_layout(int nf, int ld = 0, int mode = 0) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
@@ -63,15 +82,19 @@ __host__ __device__ inline TcLayout tc_layout(int nf, int stg_ld = 0) {
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
     L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
-    L.mbar = L.vec + (5 * 128 + 1104) * 4;
-    L.holder = L.mbar + 16;
+    L.mbar = L.vec + (5 * 128 + 1104) * 4;   // [0..1] MMA stages, [2..3] TMA staging tiles
+    L.holder = L.mbar + 32;
     L.stg = L.holder + 16;
-    L.total = L.stg + KCH * stg_ld * 4;
+    if (mode == 2) L.stg = (L.stg + 127) & ~127;
+    L.total = L.stg + (mode == 1 ? KCH * ld * 4 : mode == 2 ? NSTG * (KCH / 4) * tma_group_bytes(ld) : 0);
     return L;
 }
 
-template <bool PF>
-__global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a, int ntc) {
+template <int PFM>
+__global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (PFM == 1 ? 4 : 5))
+    k_sweep_tc(SweepArgs a, int ntc, const __grid_constant__ CUtensorMap tmap) {
+    constexpr bool PF = PFM == 1;
+    constexpr bool TM = PFM == 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -79,7 +102,7 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
     const uint32_t sbase = raw + pad;
     const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const TcLayout L = tc_layout(nf, PF ? a.ld : 0);
+    const TcLayout L = tc_layout(nf, a.ld, PFM);
     float *A = reinterpret_cast<float *>(base + L.A);
     const float *stg = reinterpret_cast<const float *>(base + L.stg);
     float *vec = reinterpret_cast<float *>(base + L.vec);
@@ -87,11 +110,18 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
     float *part = vec + 640;   // residual partials (residual phase)
     float *work = vec + 640;   // Cholesky panel scratch (factorisation phase)
     const uint32_t mbar[2] = {sbase + L.mbar, sbase + L.mbar + 8};
+    const uint32_t sbar[2] = {sbase + L.mbar + 16, sbase + L.mbar + 24};   // TMA staging tiles (NSTG used)
     uint32_t *holder = reinterpret_cast<uint32_t *>(base + L.holder);
+    const int gsf = tma_group_bytes(a.ld) / 4;           // floats between row groups (TMA tiles)
+    const int stgf = (KCH / 4) * gsf;                    // floats per TMA staging tile
 
     if (t == 0) {
         mbar_init(mbar[0], 1);
         mbar_init(mbar[1], 1);
+        if constexpr (TM) {
+            mbar_init(sbar[0], 1);
+            if (NSTG > 1) mbar_init(sbar[1], 1);
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -100,6 +130,8 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
     const uint32_t idesc = idesc_bf16_f32_mn((uint32_t)ntc);
     const float *F = reinterpret_cast<const float *>(a.F);
     uint32_t phase[2] = {0u, 0u};
+    uint32_t sphase = 0u;   // TMA staging tiles: parity of the next completion (bit s: tile s)
+    uint32_t spend = 0u;    // ... and whether a gather into it is in flight (bit s)
     bool bail = false;
 
     for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {  // one row per CTA (grid = rows)
@@ -143,9 +175,36 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                 for (int q = 0; q < 8; ++q) {
                     const int64_t e = beg + (int64_t)ch * KCH + warp + 4 * q;
                     const bool in = ch < nch && e < beg + n;
-                    oj[q] = in ? a.idx[e] : -1;
+                    // TMA: the rows arrive by id in the staging tile; only
+                    // whether the rating exists matters here
+                    oj[q] = in ? (TM ? 0 : a.idx[e]) : -1;
                     orr[q] = in ? a.val[e] : 0.0f;
                 }
+            };
+            // TMA: gather chunk ch's factor rows into staging tile sg (warp 0:
+            // lane g < 8 copies rows 4 g .. 4 g + 3; past the row's end, row 0
+            // stands in, in bounds and unused)
+            // the ids of the four rows lane g < 8 of warp 0 gathers for chunk ch
+            auto tma_ids = [&](int ch, int32_t (&y)[4]) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t e = beg + (int64_t)ch * KCH + 4 * lane + i;
+                    y[i] = (warp == 0 && lane < KCH / 4 && ch < nch && e < beg + n) ? a.idx[e] : 0;
+                }
+            };
+            int32_t ty[4];   // TMA: ids of the next chunk to gather, loaded a chunk early
+            auto tma_chunk = [&](int ch, int sg, const int32_t (&y)[4]) {
+                if (warp == 0) {
+                    const uint32_t bar = sg ? sbar[1] : sbar[0];
+                    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(KCH * a.ld * 4));
+                    __syncwarp();
+                    if (lane < KCH / 4) {
+                        fence_proxy_async_smem();
+                        tma_gather4(sbase + (uint32_t)L.stg + (uint32_t)((sg * stgf + lane * gsf) * 4), &tmap, 0,
+                                    y[0], y[1], y[2], y[3], bar);
+                    }
+                }
+                spend |= 1u << sg;
             };
             // PF: copy the factor rows of ids jj into the staging tile (row k =
             // warp + 4 q, this lane's 16 bytes: the lane later reads only those)
@@ -162,8 +221,17 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                 stage_rows(nj);
                 fetch(1, nnj, nnr);
             }
+            if constexpr (TM) {
+                for (int c0 = 0; c0 < NSTG && c0 < nch; ++c0) {
+                    tma_ids(c0, ty);
+                    tma_chunk(c0, c0, ty);
+                }
+            }
             for (int ch = 0; ch < nch; ++ch) {
                 const int st = ch & 1;
+                bool swait = true;   // TMA: this chunk's rows arrived in time
+                const int sg = ch % NSTG;   // TMA: this chunk's staging tile
+                if constexpr (TM) tma_ids(ch + NSTG, ty);   // in flight while this chunk is split
                 if (pend[st]) {  // the MMAs of chunk ch-2 still read stage st
                     const bool w = mbar_wait_bounded(mbar[st], phase[st], a.wait_ns);
                     if (__syncthreads_or(!w)) { bail = true; break; }
@@ -192,10 +260,17 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                 {
                     float f[8][4];
                     if constexpr (PF) cp_async_wait_all();  // this lane's copies of chunk ch
+                    if constexpr (TM) {
+                        swait = mbar_wait_bounded(sg ? sbar[1] : sbar[0], (sphase >> sg) & 1u, a.wait_ns);
+                        sphase ^= 1u << sg;
+                        spend &= ~(1u << sg);
+                    }
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         if (cj[q] >= 0 && act) {
-                            if constexpr (PF) ld4f(stg + (warp + 4 * q) * a.ld + 4 * lane, f[q]);
+                            const int k = warp + 4 * q;
+                            if constexpr (PF) ld4f(stg + k * a.ld + 4 * lane, f[q]);
+                            else if constexpr (TM) ld4f(stg + sg * stgf + (k >> 2) * gsf + (k & 3) * a.ld + 4 * lane, f[q]);
                             else ld4f(F + (int64_t)cj[q] * a.ld + 4 * lane, f[q]);
                         } else {
                             f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
@@ -251,7 +326,9 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                     }
                 }
                 fence_proxy_async_smem();
-                __syncthreads();
+                // every thread has read staging tile st and written stage st;
+                // a TMA wait that ran out is noticed by all
+                if (__syncthreads_or(!swait)) { bail = true; break; }
                 if (t == 0 && !a.withhold) {
                     tc_fence_after();
                     const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
@@ -266,6 +343,10 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                     tc_commit(mbar[st]);
                 }
                 pend[st] = 1;
+                // staging tile sg is free (every thread read it before the
+                // barrier): the rows of chunk ch + NSTG go there
+                if constexpr (TM)
+                    if (ch + NSTG < nch) tma_chunk(ch + NSTG, sg, ty);
             }
             if constexpr (PF) cp_async_wait_all();  // nothing in flight past the gather
             if (!bail) {
@@ -286,6 +367,10 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
                 if (t == 0 && !a.withhold)
                     for (int s = 0; s < 2; ++s)
                         if (pend[s]) (void)mbar_wait_bounded(mbar[s], phase[s], a.wait_ns);
+                // TMA gathers still in flight write this CTA's staging tiles
+                if (t == 0)
+                    for (int s = 0; s < NSTG; ++s)
+                        if ((spend >> s) & 1u) (void)mbar_wait_bounded(sbar[s], (sphase >> s) & 1u, a.wait_ns);
                 __syncthreads();
                 break;
             }
@@ -370,16 +455,56 @@ __global__ void __launch_bounds__(TC_THREADS, PF ? 4 : 5) k_sweep_tc(SweepArgs a
     if (bail && t == 0) atomicAdd(a.timeout, 1);
 }
 
-template <bool PF>
+// tensor map of the fixed side F for the TMA gathers: nF rows of ld FP32
+// values, one row per box (tile::gather4 takes four of them)
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+als_status fixed_side_map(const SweepArgs &a, CUtensorMap *m) {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    });
+    if (!g_encode) {
+        als_set_error("sweep: cuTensorMapEncodeTiled is not available");
+        return ALS_ENOTSUP;
+    }
+    const cuuint64_t gdim[2] = {(cuuint64_t)a.ld, (cuuint64_t)a.nF};
+    const cuuint64_t gstride[1] = {(cuuint64_t)a.ld * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)a.ld, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(a.F), gdim, gstride, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        als_set_error("sweep: cuTensorMapEncodeTiled failed for the fixed side");
+        return ALS_ECUDA;
+    }
+    return ALS_OK;
+}
+
+template <int PFM>
 als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     if (a.nrows <= 0) return ALS_OK;
-    const TcLayout L = tc_layout(a.nf, PF ? a.ld : 0);
-    // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; PF ~54 KB: 4
+    const TcLayout L = tc_layout(a.nf, a.ld, PFM);
+    // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; cp.async
+    // prefetching ~54 KB: 4; TMA-fed ~67 KB: 3
     size_t smem = (size_t)L.total + 1024;
-    if (raise_smem_limit((const void *)k_sweep_tc<PF>, smem) != ALS_OK) return ALS_ECUDA;
+    if (raise_smem_limit((const void *)k_sweep_tc<PFM>, smem) != ALS_OK) return ALS_ECUDA;
     // the whole L1/shared array as shared memory, so that 5 CTAs fit per SM
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PFM>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    if (PFM == 2) {
+        als_status s = fixed_side_map(a, &tm);
+        if (s != ALS_OK) return s;
+    }
     // One CTA per row (rows in degree-descending order): the hardware keeps as
     // many CTAs resident per SM as shared memory and registers allow, and
     // each holds its 128 TMEM columns only from its Gram to the read-out.
@@ -390,9 +515,9 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
         return ALS_ENOTSUP;
     }
     cudaStream_t st = a.stream ? a.stream : c->stream;
-    kt_begin(c, PF ? KT_TC_PF : KT_TC, st);
-    k_sweep_tc<PF><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc);
-    kt_end(c, PF ? KT_TC_PF : KT_TC, st);
+    kt_begin(c, PFM ? KT_TC_PF : KT_TC, st);
+    k_sweep_tc<PFM><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, tm);
+    kt_end(c, PFM ? KT_TC_PF : KT_TC, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
@@ -408,16 +533,19 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
     const int ntc = (a.nf + 15) / 16 * 16;
     // split-row segments are long: all prefetching; otherwise the first npf
     // rows of the order (the heaviest), then the rest
-    if (a.seg_out) return launch_tc<true>(c, a, ntc);
+    // the heavy rows' gather: TMA-fed when the context asks for it and the
+    // fixed side's extent is known, else cp.async
+    const bool tma = c->gather_tma && a.nF > 0;
+    if (a.seg_out) return tma ? launch_tc<2>(c, a, ntc) : launch_tc<1>(c, a, ntc);
     const int64_t npf = a.order ? std::max<int64_t>(0, std::min(a.npf, a.nrows)) : 0;
     if (npf > 0) {
         SweepArgs h = a;
         h.nrows = npf;
-        als_status s = launch_tc<true>(c, h, ntc);
+        als_status s = tma ? launch_tc<2>(c, h, ntc) : launch_tc<1>(c, h, ntc);
         if (s != ALS_OK) return s;
     }
     SweepArgs l = a;
     l.order = a.order ? a.order + npf : nullptr;
     l.nrows = a.nrows - npf;
-    return launch_tc<false>(c, l, ntc);
+    return launch_tc<0>(c, l, ntc);
 }

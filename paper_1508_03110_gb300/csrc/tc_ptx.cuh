@@ -42,6 +42,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
     return true;
 }
 
+// arrive on the barrier and add tx_bytes to the bytes its phase waits for
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t addr, uint32_t tx_bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(addr),
+                 "r"(tx_bytes)
+                 : "memory");
+}
+
+// ---- TMA ------------------------------------------------------------------------
+// Four rows y0..y3 of a 2-D tensor map whose box is one row (tile::gather4),
+// starting at column x (0 here: 16-byte aligned), into dst (shared, 128-byte
+// aligned; the rows land one after the other); completion is counted on the
+// mbarrier in bytes.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void *tmap, int32_t x, int32_t y0, int32_t y1,
+                                            int32_t y2, int32_t y3, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(mbar)
+        : "memory");
+}
+
 // ---- shared-memory stores ---------------------------------------------------
 __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
     asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
