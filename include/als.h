@@ -391,6 +391,8 @@ ALS_API void als_server_destroy(als_server *srv);
  *   gather_tma     tensor-core sweep, rows of >= 256 ratings: their factor rows
  *                  are gathered two chunks ahead by TMA (tile::gather4, 1)
  *                  or one chunk ahead by cp.async (0)
+ *   tc_chunk       tensor-core sweep, rows below 256 ratings: ratings per
+ *                  gather chunk, 16 (a smaller ring: 7 CTAs per SM) or 32 (5)
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t heavy_min;        /* default 512    */
@@ -401,6 +403,7 @@ typedef struct {
     int32_t gram_path;        /* in use         */
     int32_t dual_max;         /* default 64     */
     int32_t gather_tma;       /* default 0      */
+    int32_t tc_chunk;         /* default 32     */
 } als_launch;
 
 ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);

@@ -1108,6 +1108,7 @@ void fill_launch(const als_ctx *c, als_launch *o) {
     o->gram_path = c->f64 ? ALS_GRAM_FMA : (c->use_tc ? ALS_GRAM_TC : ALS_GRAM_FMA);
     o->dual_max = c->dual_max;
     o->gather_tma = c->gather_tma;
+    o->tc_chunk = c->tc_chunk16 ? 16 : 32;
 }
 
 // apply launch shapes (validated by the caller); rebuilds what depends on them
@@ -1131,6 +1132,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
     }
     c->dual_max = l.dual_max;
     c->gather_tma = l.gather_tma;
+    c->tc_chunk16 = l.tc_chunk == 16;
     count_sweep_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
@@ -1138,7 +1140,8 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
 
 bool launch_valid(const als_ctx *c, const als_launch &l) {
     if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
-        l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX || l.gather_tma < 0 || l.gather_tma > 1)
+        l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX || l.gather_tma < 0 || l.gather_tma > 1 ||
+        (l.tc_chunk != 16 && l.tc_chunk != 32))
         return false;
     if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
     if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
@@ -1157,7 +1160,7 @@ extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
     if (!c || !in || !launch_valid(c, *in)) {
         als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
                       "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64, "
-                      "gather_tma 0 or 1)");
+                      "gather_tma 0 or 1, tc_chunk 16 or 32)");
         return ALS_EINVAL;
     }
     return apply_launch(c, *in);
@@ -1236,6 +1239,12 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
         for (int g : {0, 1}) {
             als_launch cand = cur;
             cand.gather_tma = g;
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+        // the other rows' chunk: 16 ratings (7 CTAs per SM) or 32 (5)
+        for (int kc : {16, 32}) {
+            als_launch cand = cur;
+            cand.tc_chunk = kc;
             if ((s = trial(cand, false, best)) != ALS_OK) return s;
         }
     }

@@ -47,9 +47,11 @@
 namespace {
 
 constexpr int TC_THREADS = 128;
-constexpr int KCH = 32;                          // ratings per chunk
-constexpr int TILE_BYTES = KCH * ALS_TC_LD * 2;  // 8 KB: one BF16 tile (H or L)
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;      // H and L
+// ratings per chunk: 32 for the heavy rows' variants, 16 for the rest (a
+// smaller ring, so that more CTAs fit per SM); a tile (H or L) is KC x 128
+// BF16 values, a stage H and L
+__host__ __device__ constexpr int tile_bytes(int kc) { return kc * ALS_TC_LD * 2; }
+__host__ __device__ constexpr int stage_bytes(int kc) { return 2 * tile_bytes(kc); }
 constexpr int NSTAGE = 2;
 constexpr uint32_t LBO = 1024;  // byte distance between the two 64-wide MN atoms
 constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
@@ -71,13 +73,13 @@ struct TcLayout {
     int ring, A, vec, mbar, holder, stg, total;
 };
 
-// mode 1: a staging tile of KCH factor rows of ld floats; mode 2: NSTG TMA
-// staging tiles of KCH / 4 row groups
-__host__ __device__ inline TcLayout tc_layout(int nf, int ld = 0, int mode = 0) {
+// mode 1: a staging tile of kc factor rows of ld floats; mode 2: NSTG TMA
+// staging tiles of kc / 4 row groups
+__host__ __device__ inline TcLayout tc_layout(int nf, int ld, int mode, int kc) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
-    int big = NSTAGE * STAGE_BYTES;
+    int big = NSTAGE * stage_bytes(kc);
     const int a_bytes = nf * (nf + 1) / 2 * 4;  // packed lower triangle
     if (a_bytes > big) big = a_bytes;
     big = (big + 15) & ~15;
@@ -86,15 +88,47 @@ __host__ __device__ inline TcLayout tc_layout(int nf, int ld = 0, int mode = 0) 
     L.holder = L.mbar + 32;
     L.stg = L.holder + 16;
     if (mode == 2) L.stg = (L.stg + 127) & ~127;
-    L.total = L.stg + (mode == 1 ? KCH * ld * 4 : mode == 2 ? NSTG * (KCH / 4) * tma_group_bytes(ld) : 0);
+    L.total = L.stg + (mode == 1 ? kc * ld * 4 : mode == 2 ? NSTG * (kc / 4) * tma_group_bytes(ld) : 0);
     return L;
 }
 
-template <int PFM>
-__global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (PFM == 1 ? 4 : 5))
+// d[q] <- sum of d[q] over the warp for Q = 8 (warp_allsum8) or Q = 4 values:
+// two halving exchanges leave each lane one value summed over 4 lanes, three
+// more finish it over the warp, and 4 reads gather the totals
+template <int Q>
+__device__ __forceinline__ void warp_allsum_q(float (&d)[Q], int lane) {
+    if constexpr (Q == 8) {
+        warp_allsum8(d, lane);
+    } else {
+        static_assert(Q == 4, "chunks of 16 or 32 ratings");
+        const bool b4 = lane & 16, b3 = lane & 8;
+        float e2[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            e2[i] = (b4 ? d[i + 2] : d[i]) + __shfl_xor_sync(0xffffffffu, b4 ? d[i] : d[i + 2], 16);
+        float e1 = (b3 ? e2[1] : e2[0]) + __shfl_xor_sync(0xffffffffu, b3 ? e2[0] : e2[1], 8);
+        e1 += __shfl_xor_sync(0xffffffffu, e1, 4);
+        e1 += __shfl_xor_sync(0xffffffffu, e1, 2);
+        e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = __shfl_sync(0xffffffffu, e1, ((q >> 1) & 1) * 16 + (q & 1) * 8);
+    }
+}
+
+// resident CTAs per SM the register budget is set for
+__host__ __device__ constexpr int tc_min_blocks(int pfm, int kc) {
+    return pfm == 2 ? (NSTG == 1 ? 4 : 3) : (pfm == 1 ? 4 : (kc == 16 ? 7 : 5));
+}
+
+template <int PFM, int KC>
+__global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
     k_sweep_tc(SweepArgs a, int ntc, const __grid_constant__ CUtensorMap tmap) {
     constexpr bool PF = PFM == 1;
     constexpr bool TM = PFM == 2;
+    constexpr int KCH = KC;
+    constexpr int Q = KC / 4;                 // ratings of a chunk per warp
+    constexpr int TILE_BYTES = tile_bytes(KC);
+    constexpr int STAGE_BYTES = stage_bytes(KC);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -102,7 +136,7 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
     const uint32_t sbase = raw + pad;
     const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const TcLayout L = tc_layout(nf, a.ld, PFM);
+    const TcLayout L = tc_layout(nf, a.ld, PFM, KC);
     float *A = reinterpret_cast<float *>(base + L.A);
     const float *stg = reinterpret_cast<const float *>(base + L.stg);
     float *vec = reinterpret_cast<float *>(base + L.vec);
@@ -165,14 +199,14 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
             //      while the chunk's copies and MMAs are in flight -------------
             const int nch = (n + KCH - 1) / KCH;
             int pend[2] = {0, 0};
-            // ids and ratings of this warp's ratings k = warp + 4 q (q < 8) of
+            // ids and ratings of this warp's ratings k = warp + 4 q (q < Q) of
             // the next chunk, fetched one chunk ahead (PF: two ahead, the next
             // chunk's rows being copied already)
-            int32_t nj[8], nnj[8];
-            float nr[8], nnr[8];
-            auto fetch = [&](int ch, int32_t (&oj)[8], float (&orr)[8]) {
+            int32_t nj[Q], nnj[Q];
+            float nr[Q], nnr[Q];
+            auto fetch = [&](int ch, int32_t (&oj)[Q], float (&orr)[Q]) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < Q; ++q) {
                     const int64_t e = beg + (int64_t)ch * KCH + warp + 4 * q;
                     const bool in = ch < nch && e < beg + n;
                     // TMA: the rows arrive by id in the staging tile; only
@@ -208,9 +242,9 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
             };
             // PF: copy the factor rows of ids jj into the staging tile (row k =
             // warp + 4 q, this lane's 16 bytes: the lane later reads only those)
-            auto stage_rows = [&](const int32_t (&jj)[8]) {
+            auto stage_rows = [&](const int32_t (&jj)[Q]) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
+                for (int q = 0; q < Q; ++q)
                     if (jj[q] >= 0 && act)
                         cp_async16(sbase + (uint32_t)L.stg + (uint32_t)(((warp + 4 * q) * a.ld + 4 * lane) * 4),
                                    F + (int64_t)jj[q] * a.ld + 4 * lane);
@@ -238,16 +272,16 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                     phase[st] ^= 1u;
                     pend[st] = 0;
                 }
-                int32_t cj[8];
-                float cr[8];
+                int32_t cj[Q];
+                float cr[Q];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < Q; ++q) {
                     cj[q] = nj[q];
                     cr[q] = nr[q];
                 }
                 if constexpr (PF) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < Q; ++q) {
                         nj[q] = nnj[q];
                         nr[q] = nnr[q];
                     }
@@ -258,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                 // each factor row is read once, in FP32: it feeds the residual
                 // at u0 and, split into BF16 hi + lo, the operand tiles of stage st
                 {
-                    float f[8][4];
+                    float f[Q][4];
                     if constexpr (PF) cp_async_wait_all();  // this lane's copies of chunk ch
                     if constexpr (TM) {
                         swait = mbar_wait_bounded(sg ? sbar[1] : sbar[0], (sphase >> sg) & 1u, a.wait_ns);
@@ -266,7 +300,7 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                         spend &= ~(1u << sg);
                     }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < Q; ++q) {
                         if (cj[q] >= 0 && act) {
                             const int k = warp + 4 * q;
                             if constexpr (PF) ld4f(stg + k * a.ld + 4 * lane, f[q]);
@@ -276,9 +310,9 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                             f[q][0] = f[q][1] = f[q][2] = f[q][3] = 0.0f;
                         }
                     }
-                    float d[8];
+                    float d[Q];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < Q; ++q) {
                         d[q] = uu[0] * f[q][0];
 #pragma unroll
                         for (int i = 1; i < 4; ++i) d[q] = fmaf(uu[i], f[q][i], d[q]);
@@ -287,13 +321,13 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                     // used them all): the next chunk's copies may overwrite them
                     if constexpr (PF)
                         if (ch + 1 < nch) stage_rows(nj);
-                    warp_allsum8(d, lane);
+                    warp_allsum_q(d, lane);
                     {
-                        // the chunk's 8 terms in plain FP32, then one compensated
+                        // the chunk's Q terms in plain FP32, then one compensated
                         // add into the row's running sum
                         float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
+                        for (int q = 0; q < Q; ++q) {
                             const float er = cj[q] >= 0 ? cr[q] - d[q] : 0.0f;
 #pragma unroll
                             for (int i = 0; i < 4; ++i) cs[i] = fmaf(er, f[q][i], cs[i]);
@@ -304,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS, PFM == 2 ? (NSTG == 1 ? 4 : 3) : (
                     if (act) {
                         const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
+                        for (int q = 0; q < Q; ++q) {
                             const int k = warp + 4 * q;   // K index (rating within the chunk)
                             const int qq = lane >> 1;     // 16-byte column chunk: factors 8 qq .. 8 qq + 7
                             const uint32_t off = (uint32_t)(k >> 3) * SBO + (uint32_t)(qq >> 3) * LBO +
@@ -488,16 +522,16 @@ als_status fixed_side_map(const SweepArgs &a, CUtensorMap *m) {
     return ALS_OK;
 }
 
-template <int PFM>
+template <int PFM, int KC>
 als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     if (a.nrows <= 0) return ALS_OK;
-    const TcLayout L = tc_layout(a.nf, a.ld, PFM);
+    const TcLayout L = tc_layout(a.nf, a.ld, PFM, KC);
     // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; cp.async
     // prefetching ~54 KB: 4; TMA-fed ~67 KB: 3
     size_t smem = (size_t)L.total + 1024;
-    if (raise_smem_limit((const void *)k_sweep_tc<PFM>, smem) != ALS_OK) return ALS_ECUDA;
-    // the whole L1/shared array as shared memory, so that 5 CTAs fit per SM
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PFM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    if (raise_smem_limit((const void *)k_sweep_tc<PFM, KC>, smem) != ALS_OK) return ALS_ECUDA;
+    // the whole L1/shared array as shared memory, so that 5-7 CTAs fit per SM
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PFM, KC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     CUtensorMap tm;
     std::memset(&tm, 0, sizeof tm);
@@ -516,7 +550,7 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     }
     cudaStream_t st = a.stream ? a.stream : c->stream;
     kt_begin(c, PFM ? KT_TC_PF : KT_TC, st);
-    k_sweep_tc<PFM><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, tm);
+    k_sweep_tc<PFM, KC><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, tm);
     kt_end(c, PFM ? KT_TC_PF : KT_TC, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
@@ -536,16 +570,18 @@ als_status launch_sweep_tc(als_ctx *c, const SweepArgs &a) {
     // the heavy rows' gather: TMA-fed when the context asks for it and the
     // fixed side's extent is known, else cp.async
     const bool tma = c->gather_tma && a.nF > 0;
-    if (a.seg_out) return tma ? launch_tc<2>(c, a, ntc) : launch_tc<1>(c, a, ntc);
+    if (a.seg_out) return tma ? launch_tc<2, 32>(c, a, ntc) : launch_tc<1, 32>(c, a, ntc);
     const int64_t npf = a.order ? std::max<int64_t>(0, std::min(a.npf, a.nrows)) : 0;
     if (npf > 0) {
         SweepArgs h = a;
         h.nrows = npf;
-        als_status s = tma ? launch_tc<2>(c, h, ntc) : launch_tc<1>(c, h, ntc);
+        als_status s = tma ? launch_tc<2, 32>(c, h, ntc) : launch_tc<1, 32>(c, h, ntc);
         if (s != ALS_OK) return s;
     }
     SweepArgs l = a;
     l.order = a.order ? a.order + npf : nullptr;
     l.nrows = a.nrows - npf;
-    return launch_tc<0>(c, l, ntc);
+    // the other rows: 32-rating chunks (5 CTAs per SM), or 16 (a 16 KB ring,
+    // 7 CTAs per SM: measured 5% slower at ML20M size, kept as a launch shape)
+    return c->tc_chunk16 ? launch_tc<0, 16>(c, l, ntc) : launch_tc<0, 32>(c, l, ntc);
 }

@@ -58,3 +58,24 @@ def test_tma_gather_fullsize_equals_cp_async():
     a, b = _pair(r, r.n_f, dict(heavy_min=1024, grid_mult=64, split_min=65536, seg_len=4096, dual_max=64), 2, x0)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+def test_chunk_sizes_agree():
+    """Rows below 256 ratings gathered in chunks of 16 ratings (7 CTAs per SM)
+    or 32: the same Gram matrices (the same MMAs in the same order); the FP32
+    residual's compensated sum is grouped per chunk, so the rows agree to the
+    refinement's FP32 floor, far inside the mixed form's bound."""
+    from paper_1508_03110_gb300 import ALS
+    r = synth.make_config("tiny")
+    n_f = 100
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 8)
+    out = {}
+    for kc in (16, 32):
+        with ALS(r.n_u, r.n_m, r.rows, r.cols, r.vals, n_f, r.lam, precision="mixed", gram_path="tc") as m:
+            m.set_launch(tc_chunk=kc)
+            assert m.get_launch()["tc_chunk"] == kc
+            m.set_x(x0)
+            m.sweep(1)
+            out[kc] = m.get_x().reshape(-1, n_f)
+    err = np.linalg.norm(out[16] - out[32], axis=1)
+    assert np.all(err <= 1e-6 * np.linalg.norm(out[32], axis=1) + 1e-30)
