@@ -598,9 +598,9 @@ def run_scale(args):
 # digits) of the kernel's sources when it was captured.  A figure is reported
 # only while those sources are unchanged.
 # Captured on a GB300 (profiles/sweep_dram_traffic_ml20m.md): the 4 launches
-# of k_sweep_tc in one sweep read 634.2 MB and wrote 15.4 MB; the 2 launches
-# of k_sweep_dual read 116.4 MB and wrote 35.6 MB.
-TRAFFIC = {"k_sweep_tc": ("aaebd828c8ee6793", 649_568_512), "k_sweep_dual": ("91b1801e7dcbadbf", 152_011_520)}
+# of k_sweep_tc in one sweep read 633.0 MB and wrote 15.3 MB; the 2 launches
+# of k_sweep_dual read 116.2 MB and wrote 35.5 MB.
+TRAFFIC = {"k_sweep_tc": ("1beaf3dee73b068b", 648311040), "k_sweep_dual": ("91b1801e7dcbadbf", 151659264)}
 TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh"),
                    "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh")}
 
