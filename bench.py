@@ -25,7 +25,7 @@ s_to_tol = seconds (device work of the iterations, each context autotuned
          timed, as in the paper), with (1/N)|g_k| of the paper's stopping
          test beside each figure.
 
-`--impl reference` times the oracle alone (the reference arm of this build).
+`--impl reference` times the FP64 oracle alone on the host cores.
 Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N` runs N independent
 replicas (one problem fits one GPU and a replica needs no exchange); value is
 the sum over ranks and the time the max over ranks.
