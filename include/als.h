@@ -393,6 +393,10 @@ ALS_API void als_server_destroy(als_server *srv);
  *                  or one chunk ahead by cp.async (0)
  *   tc_chunk       tensor-core sweep, rows below 256 ratings: ratings per
  *                  gather chunk, 16 (a smaller ring: 7 CTAs per SM) or 32 (5)
+ *   chol_tc        tensor-core sweep: each row's matrix is factored in shared
+ *                  memory on the CUDA cores (0), or in place in TMEM by
+ *                  panels of 16 columns whose trailing updates are tcgen05
+ *                  MMAs (1)
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t heavy_min;        /* default 512    */
@@ -404,6 +408,7 @@ typedef struct {
     int32_t dual_max;         /* default 64     */
     int32_t gather_tma;       /* default 0      */
     int32_t tc_chunk;         /* default 32     */
+    int32_t chol_tc;          /* default 0      */
 } als_launch;
 
 ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);

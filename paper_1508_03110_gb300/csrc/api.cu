@@ -129,6 +129,7 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.timeout = c->dflags + 7;
     a.nbig = c->sweep_big[side];
     a.ndual = c->sweep_dual[side];
+    a.ndual_small = c->sweep_dual_small[side];
     a.npf = c->sweep_pf[side];
     a.dual_nmax = std::min(c->dual_max, c->nf);
     const int64_t H = c->nsplit[side];
@@ -958,11 +959,12 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
                      [&](int32_t x, int32_t y) { return hp[x + 1] - hp[x] > hp[y + 1] - hp[y]; });
     const int T = std::min(c->dual_max, c->nf);
     const bool dual = c->use_tc && !c->f64 && c->cfg.lambda > 0.0 && T > 0;
-    int64_t npf = 0, ndual = 0;
+    int64_t npf = 0, ndual = 0, nsmall = 0;
     for (int64_t q = 0; q < n_req; ++q) {
         const int64_t d = hp[hord[q] + 1] - hp[hord[q]];
         if (d >= ALS_TC_PF_MIN) ++npf;
         if (dual && d <= T) ++ndual;
+        if (dual && d <= std::min(T, ALS_DUAL_SMALL)) ++nsmall;
     }
     if ((s = ctx_alloc(c, (void **)&dord, n_req * sizeof(int32_t))) != ALS_OK) { cleanup(); return s; }
     TRY(cudaMemcpyAsync(dord, hord.data(), n_req * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
@@ -974,6 +976,7 @@ extern "C" als_status als_foldin(als_ctx *c, int64_t n_req, const int64_t *req_p
     a.nrows = n_req;
     a.npf = npf;
     a.ndual = ndual;
+    a.ndual_small = nsmall;
     a.dual_nmax = dual ? T : 0;
     a.F = mblk(c, c->X);
     a.nF = c->n_m;
@@ -1109,6 +1112,7 @@ void fill_launch(const als_ctx *c, als_launch *o) {
     o->dual_max = c->dual_max;
     o->gather_tma = c->gather_tma;
     o->tc_chunk = c->tc_chunk16 ? 16 : 32;
+    o->chol_tc = c->chol_tc;
 }
 
 // apply launch shapes (validated by the caller); rebuilds what depends on them
@@ -1133,6 +1137,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
     c->dual_max = l.dual_max;
     c->gather_tma = l.gather_tma;
     c->tc_chunk16 = l.tc_chunk == 16;
+    c->chol_tc = l.chol_tc;
     count_sweep_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
@@ -1141,7 +1146,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
 bool launch_valid(const als_ctx *c, const als_launch &l) {
     if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
         l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX || l.gather_tma < 0 || l.gather_tma > 1 ||
-        (l.tc_chunk != 16 && l.tc_chunk != 32))
+        (l.tc_chunk != 16 && l.tc_chunk != 32) || l.chol_tc < 0 || l.chol_tc > 1)
         return false;
     if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
     if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
@@ -1160,7 +1165,7 @@ extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
     if (!c || !in || !launch_valid(c, *in)) {
         als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
                       "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64, "
-                      "gather_tma 0 or 1, tc_chunk 16 or 32)");
+                      "gather_tma 0 or 1, tc_chunk 16 or 32, chol_tc 0 or 1)");
         return ALS_EINVAL;
     }
     return apply_launch(c, *in);
@@ -1245,6 +1250,13 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
         for (int kc : {16, 32}) {
             als_launch cand = cur;
             cand.tc_chunk = kc;
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+        // the rows' Cholesky: CUDA cores in shared memory, or TMEM panels
+        // with the trailing updates on the tensor core
+        for (int ct : {0, 1}) {
+            als_launch cand = cur;
+            cand.chol_tc = ct;
             if ((s = trial(cand, false, best)) != ALS_OK) return s;
         }
     }

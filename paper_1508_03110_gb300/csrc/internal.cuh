@@ -15,6 +15,7 @@
 #define ALS_TC_LD 128          // widest n_f of the tcgen05 Gram (one 128-row MMA tile)
 #define ALS_HEAVY_MIN 512      // rows at least this long get a whole CTA in the passes (default)
 #define ALS_DUAL_MAX 64        // longest row of the mixed form's light-row (n_i x n_i) solve
+#define ALS_DUAL_SMALL 32      // light rows at most this long take a smaller layout (more CTAs per SM)
 #define ALS_TC_PF_MIN 256      // tensor-core sweep: rows at least this long prefetch their factor rows
 
 // Slots of the device scalar block (double S[]).
@@ -114,12 +115,14 @@ struct als_ctx {
     int grid_mult = 32;                // pass grids: at most grid_mult x sm_count CTAs
     int sweep_bin_min = 0;             // FMA sweep, n_f <= 32: rows with >= this many ratings use a CTA (0: none)
     int64_t sweep_big[2] = {0, 0};     // ... their count per side (a prefix of the degree order)
+    int chol_tc = 0;                   // tensor-core sweep: Cholesky from TMEM, trailing updates as MMAs (1)
     int tc_chunk16 = 0;                // tensor-core sweep, rows below 256 ratings: chunks of 16 ratings (1) or 32 (0)
     int gather_tma = 0;                // tensor-core sweep: heavy rows' factor rows gathered by TMA (1)
                                        // or by cp.async (0)
     int dual_max = ALS_DUAL_MAX;       // mixed tensor-core sweep: rows of <= min(dual_max, n_f) ratings
                                        // are solved through their n_i x n_i matrix (0: none)
     int64_t sweep_dual[2] = {0, 0};    // ... their count per side (a suffix of the degree order)
+    int64_t sweep_dual_small[2] = {0, 0};  // ... of which the last ones, of <= ALS_DUAL_SMALL ratings
     int64_t sweep_pf[2] = {0, 0};      // tensor-core sweep: rows of >= ALS_TC_PF_MIN ratings after the
                                        // split rows (a prefix of the rest of the degree order)
     std::vector<int32_t> h_deg[2];     // degrees in degree order (host), filled on first use
@@ -221,6 +224,7 @@ struct SweepArgs {
     // most dual_nmax <= ALS_DUAL_MAX ratings) take the light-row solve
     int64_t ndual = 0;
     int dual_nmax = 0;
+    int64_t ndual_small = 0;   // ... the last of which have at most ALS_DUAL_SMALL ratings
     // segment mode (split heavy rows): "row" r is segment r, a slice
     // [seg_beg[r], seg_beg[r] + seg_len[r]) of the ratings of row
     // order[seg_row[r]]; the kernel writes that slice's partial Gram matrix

@@ -153,7 +153,7 @@ bool launch_batch(als_server *s, Slot &sl) {
     // rows: the heaviest take the prefetching tensor-core kernel, the
     // lightest (at most min(dual_max, n_f) ratings, lambda > 0, mixed form)
     // the light-row solve through their n_i x n_i matrix
-    int64_t npf = 0, ndual = 0;
+    int64_t npf = 0, ndual = 0, nsmall = 0;
     const int T = std::min(c->dual_max, c->nf);
     const bool dual = c->use_tc && !c->f64 && c->cfg.lambda > 0.0 && T > 0;
     for (int64_t q = 0; q < nreq; ++q) sl.horder[q] = (int32_t)q;
@@ -164,6 +164,7 @@ bool launch_batch(als_server *s, Slot &sl) {
         const int64_t d = sl.hptr[sl.horder[q] + 1] - sl.hptr[sl.horder[q]];
         if (d >= ALS_TC_PF_MIN) ++npf;
         if (dual && d <= T) ++ndual;
+        if (dual && d <= std::min(T, ALS_DUAL_SMALL)) ++nsmall;
     }
     cudaMemcpyAsync(sl.dorder, sl.horder, nreq * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream);
     SweepArgs a;
@@ -174,6 +175,7 @@ bool launch_batch(als_server *s, Slot &sl) {
     a.nrows = nreq;
     a.npf = npf;
     a.ndual = ndual;
+    a.ndual_small = nsmall;
     a.dual_nmax = dual ? T : 0;
     a.F = (const char *)c->X + (size_t)c->n_u * c->ld * c->esz;
     a.nF = c->n_m;

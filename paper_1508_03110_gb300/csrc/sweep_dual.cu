@@ -62,7 +62,8 @@ __device__ __forceinline__ float dot_sm(const float *p, const float *q, int nf4,
     return s0 + s1;
 }
 
-__global__ void __launch_bounds__(DU_THREADS, 5) k_sweep_dual(SweepArgs a, int nmax) {
+template <int MINB>
+__global__ void __launch_bounds__(DU_THREADS, MINB) k_sweep_dual(SweepArgs a, int nmax) {
     extern __shared__ __align__(16) float sm[];
     const int nf = a.nf, nf4 = (nf + 3) & ~3;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -279,6 +280,27 @@ __global__ void __launch_bounds__(DU_THREADS, 5) k_sweep_dual(SweepArgs a, int n
 
 }  // namespace
 
+namespace {
+
+// nmax <= ALS_DUAL_SMALL: a layout of ~23 KB (n_f = 100) and a register
+// budget of 72 per thread, so that 7 CTAs fit per SM; longer rows ~43 KB, 5
+template <int MINB>
+als_status launch_dual(als_ctx *c, const SweepArgs &a, int nmax) {
+    const DualLayout L = dual_layout(a.nf, nmax);
+    const size_t smem = (size_t)L.total * sizeof(float);
+    if (raise_smem_limit((const void *)k_sweep_dual<MINB>, smem) != ALS_OK) return ALS_ECUDA;
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_dual<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    cudaStream_t st = a.stream ? a.stream : c->stream;
+    kt_begin(c, KT_DUAL, st);
+    k_sweep_dual<MINB><<<(unsigned)a.nrows, DU_THREADS, smem, st>>>(a, nmax);
+    kt_end(c, KT_DUAL, st);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+}  // namespace
+
 als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
     if (a.nrows <= 0) return ALS_OK;
     if (a.nf > ALS_TC_LD || nmax < 1 || nmax > ALS_DUAL_MAX) {
@@ -289,15 +311,19 @@ als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
         als_set_error("sweep: more rows than CTAs in one launch");
         return ALS_ENOTSUP;
     }
-    const DualLayout L = dual_layout(a.nf, nmax);
-    const size_t smem = (size_t)L.total * sizeof(float);
-    if (raise_smem_limit((const void *)k_sweep_dual, smem) != ALS_OK) return ALS_ECUDA;
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_dual, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-    cudaStream_t st = a.stream ? a.stream : c->stream;
-    kt_begin(c, KT_DUAL, st);
-    k_sweep_dual<<<(unsigned)a.nrows, DU_THREADS, smem, st>>>(a, nmax);
-    kt_end(c, KT_DUAL, st);
-    ALS_CUDA_TRY(cudaGetLastError());
-    return ALS_OK;
+    if (nmax <= ALS_DUAL_SMALL) return launch_dual<7>(c, a, nmax);
+    // the rows (a suffix of the degree order) of at most ALS_DUAL_SMALL
+    // ratings in the smaller layout, the longer ones before them
+    const int64_t ns = a.order ? std::max<int64_t>(0, std::min(a.ndual_small, a.nrows)) : 0;
+    if (ns < a.nrows) {
+        SweepArgs l = a;
+        l.nrows = a.nrows - ns;
+        als_status s = launch_dual<5>(c, l, nmax);
+        if (s != ALS_OK) return s;
+    }
+    if (ns == 0) return ALS_OK;
+    SweepArgs sm = a;
+    sm.order = a.order + (a.nrows - ns);
+    sm.nrows = ns;
+    return launch_dual<7>(c, sm, ALS_DUAL_SMALL);
 }

@@ -17,9 +17,14 @@
 //      correction was not yet negligible: one CTA per segment forms its part
 //      of the FP32 residual at the new row, one CTA per row adds them, solves
 //      with the kept factor and applies the correction.
-// Accuracy: a segment's tensor-core partial accumulates at most ~seg_len
+// Accuracy: a segment's tensor-core partial accumulates at most seg_len
 // ratings in FP32 and the segments are added in FP64, so a split row's Gram
-// matrix is more accurate than a whole row's.
+// matrix is more accurate than a whole row's: its relative error is that of
+// one segment's, 2^-17 (the BF16 split) + seg_len 2^-24 (FP32 accumulation),
+// plus one FP32 rounding of the sum.  The refinement's stopping rule
+// (sw_correction_small) therefore takes min(n_i, seg_len) ratings for a
+// split row rather than n_i, so long rows stop as soon as a row of seg_len
+// ratings would.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -50,6 +55,7 @@ struct SplitArgs {
     int nf, ld;
     double lambda;
     int more;                 // mixed: corrections still allowed after this one
+    int seg_cap;              // the most ratings of any segment (seg_len)
 };
 
 constexpr int HT = 128;  // threads per CTA
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(HT) k_split_solve(SplitArgs s) {
             float *hf = s.hfac + (size_t)h * tri;
             for (int e = t; e < tri; e += HT) hf[e] = A[e];
             __syncthreads();
-            const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)n, work, t);
+            const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)(n < s.seg_cap ? n : (int64_t)s.seg_cap), work, t);
             if (t == 0) s.hflag[h] = (s.more > 0 && !small) ? 1 : 0;
         }
     }
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(HT) k_split_refine(SplitArgs s) {
     trisolve_inv128(A, nf, v1, v2, colk, t);  // starts with a barrier
     for (int k = t; k < nf; k += HT) u[k] += colk[k];
     __syncthreads();
-    const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)n, red, t);
+    const bool small = sw_correction_small<float, HT>(colk, u, nf, (int)(n < s.seg_cap ? n : (int64_t)s.seg_cap), red, t);
     if (t == 0) s.hflag[h] = (s.more > 0 && !small) ? 1 : 0;
     const float *xi = s.Xin ? reinterpret_cast<const float *>(s.Xin) + row * s.ld : nullptr;
     float *gb = s.Gbar ? reinterpret_cast<float *>(s.Gbar) + row * s.ld : nullptr;
@@ -318,11 +324,16 @@ void count_sweep_rows(als_ctx *c) {
             std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x >= ALS_TC_PF_MIN; }) - d.begin();
         c->sweep_pf[side] = std::max<int64_t>(0, heavy - c->nsplit[side]);
         c->sweep_dual[side] = 0;
+        c->sweep_dual_small[side] = 0;
         const int T = std::min(c->dual_max, c->nf);
         if (c->f64 || T <= 0 || !(c->cfg.lambda > 0.0) || c->nf > ALS_TC_LD || n == 0) continue;
         const int64_t first =
             std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x > T; }) - d.begin();
         c->sweep_dual[side] = std::max<int64_t>(0, std::min<int64_t>(n - first, n - c->nsplit[side]));
+        const int Ts = std::min(T, ALS_DUAL_SMALL);
+        const int64_t first_small =
+            std::partition_point(d.begin(), d.end(), [&](int32_t x) { return x > Ts; }) - d.begin();
+        c->sweep_dual_small[side] = std::min<int64_t>(n - first_small, c->sweep_dual[side]);
     }
 }
 
@@ -378,6 +389,7 @@ als_status split_sweep_launches(als_ctx *c, const SweepArgs &a, int side, cudaSt
     s.ld = a.ld;
     s.lambda = a.lambda;
     s.more = a.refine - 1;
+    s.seg_cap = c->seg_len;
     const size_t smem = solve_smem(a.nf, c->esz);
     if (c->f64) {
         if (raise_smem_limit((const void *)k_split_solve<double>, smem) != ALS_OK) return ALS_ECUDA;

@@ -24,6 +24,9 @@
 //      the ALS solve from u0: u <- u + A^{-1} res, res = sum_e f_e (r_e -
 //      f_e . u) - lambda n_i u in FP32 from the FP32 factors (the first
 //      residual comes from step 1).
+// With the launch shape chol_tc, steps 3-4 factor A in place in TMEM instead
+// (chol_tmem: panels of 16 columns, trailing updates as tcgen05 MMAs), and the
+// CTA holds its TMEM columns until the factorisation ends.
 // Every mbarrier wait is bounded (%globaltimer): on expiry the CTA gives each
 // stage whose MMAs may still be in flight one more bounded wait, records a
 // timeout, frees its TMEM and returns.  The rows of such a launch are not
@@ -56,6 +59,12 @@ constexpr int NSTAGE = 2;
 constexpr uint32_t LBO = 1024;  // byte distance between the two 64-wide MN atoms
 constexpr uint32_t SBO = 2048;  // byte distance between groups of 8 K rows
 constexpr int TMEM_COLS = 128;
+// the Cholesky's trailing-update operands: 128 rows x 16 BF16 K values,
+// K-major without swizzle (core matrices of 8 rows x 16 bytes: the two K
+// halves 128 bytes apart, groups of 8 rows 256 bytes apart)
+constexpr int CH_TILE = 128 * 16 * 2;
+constexpr uint32_t CH_LBO = 128;
+constexpr uint32_t CH_SBO = 256;
 
 // Variants of the gather (template PFM): 0 each lane loads its factor rows
 // from global memory; 1 (prefetching) the next chunk's rows are copied into a
@@ -70,18 +79,22 @@ constexpr int NSTG = 1;   // TMA staging tiles (gathers run NSTG chunks ahead)
 __host__ __device__ inline int tma_group_bytes(int ld) { return (4 * ld * 4 + 127) & ~127; }
 
 struct TcLayout {
-    int ring, A, vec, mbar, holder, stg, total;
+    int ring, A, ops, vec, mbar, holder, stg, total;
 };
 
 // mode 1: a staging tile of kc factor rows of ld floats; mode 2: NSTG TMA
-// staging tiles of kc / 4 row groups
-__host__ __device__ inline TcLayout tc_layout(int nf, int ld, int mode, int kc) {
+// staging tiles of kc / 4 row groups; chol_tc: room for the TMEM
+// factorisation's operand tiles after A
+__host__ __device__ inline TcLayout tc_layout(int nf, int ld, int mode, int kc, int chol_tc) {
     TcLayout L;
     L.ring = 0;
     L.A = 0;  // the FP32 matrix reuses the gather ring once the MMAs are done
     int big = NSTAGE * stage_bytes(kc);
     const int a_bytes = nf * (nf + 1) / 2 * 4;  // packed lower triangle
-    if (a_bytes > big) big = a_bytes;
+    // then the Cholesky's operand tiles (BF16 hi and lo, 128 rows x 16 K)
+    L.ops = (a_bytes + 127) & ~127;
+    const int a_end = chol_tc ? L.ops + 2 * CH_TILE : a_bytes;
+    if (a_end > big) big = a_end;
     big = (big + 15) & ~15;
     L.vec = big;  // colk, v1, v2, u, diag [5][128]; then part[4][128] / Cholesky work (aliased)
     L.mbar = L.vec + (5 * 128 + 1104) * 4;   // [0..1] MMA stages, [2..3] TMA staging tiles
@@ -115,6 +128,148 @@ __device__ __forceinline__ void warp_allsum_q(float (&d)[Q], int lane) {
     }
 }
 
+// Cholesky factorisation of A = D + lambda n I with the Gram matrix D in TMEM
+// (row m in lane m, entry j in column j), right-looking by panels of 16
+// columns; the trailing updates run on the tensor core:
+//   1. every thread loads its row's 16 entries of the panel (tcgen05.ld) and
+//      adds lambda n on the diagonal;
+//   2. the warp holding the panel's 16 diagonal rows factors the 16 x 16
+//      diagonal block in registers, one row per lane, exchanging the columns
+//      of L by shuffles, and publishes L_kk: into packed A, transposed into
+//      l11t, and 1 / L[k][k] into diag;
+//   3. every row below the block forms its row of L21 = A21 L_kk^-T by
+//      forward substitution, stores it into packed A and, split into BF16
+//      hi + lo, into a K-major operand tile (zero rows elsewhere);
+//   4. one thread issues D[:, c0 + 16 :] -= L21 L21^T as tcgen05.mma with A
+//      negated, hi hi^T + hi lo^T + lo hi^T (lo lo^T dropped, as in the
+//      Gram), committed to an mbarrier that the next panel waits on.
+// So the O(n_f^3) part of the factorisation is three MMAs per panel, and
+// no FP32 trailing update is left on the CUDA cores.  On return A's lower
+// triangle holds L and diag[k] = 1 / L[k][k] (as chol_blocked128 leaves
+// them); false (in every thread) on a non-positive pivot; bail set when a
+// bounded wait ran out (the last panel's MMAs may still be in flight: the
+// caller waits once more before freeing TMEM).  l11t: 257 floats of scratch.
+__device__ __forceinline__ bool chol_tmem(uint32_t tmem, int nf, int ntc, float lam_n, float *A, float *diag, float *l11t,
+                          uint32_t ops, uint32_t mbar, uint32_t &phase, uint64_t wait_ns, bool withhold, int t,
+                          bool &bail) {
+    const int warp = t >> 5, lane = t & 31;
+    int *flag = reinterpret_cast<int *>(l11t + 256);
+    const uint32_t rowoff = (uint32_t)(t >> 3) * CH_SBO + (uint32_t)(t & 7) * 16;
+    for (int c0 = 0; c0 < nf; c0 += 16) {
+        if (c0 > 0) {  // the previous panel's update has reached TMEM
+            const bool w = mbar_wait_bounded(mbar, phase, wait_ns);
+            if (__syncthreads_or(!w)) {
+                bail = true;
+                return false;
+            }
+            phase ^= 1u;
+        }
+        tc_fence_after();
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        const int li = t - c0;
+        // rows and columns past n_f: the identity in the diagonal block, zero
+        // elsewhere
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (t >= nf) v[j] = (li == j) ? 1.0f : 0.0f;
+            else if (c0 + j >= nf) v[j] = 0.0f;
+            else if (li == j) v[j] += lam_n;
+        }
+        if (warp == (c0 >> 5)) {
+            const int base = c0 & 31;
+            const bool inb = li >= 0 && li < 16;
+            bool bad = false;
+            float rdo = 1.0f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float pj = __shfl_sync(0xffffffffu, v[j], base + j);
+                bad |= !(pj > 0.0f);
+                const float rj = rsqrtf(pj);
+                if (inb && li == j) {
+                    v[j] = pj * rj;
+                    rdo = rj;
+                } else if (inb && li > j) {
+                    v[j] *= rj;
+                }
+#pragma unroll
+                for (int k = 1; k < 16; ++k) {
+                    if (k <= j) continue;
+                    const float lk = __shfl_sync(0xffffffffu, v[j], base + k);
+                    if (inb && li >= k) v[k] = fmaf(-v[j], lk, v[k]);
+                }
+            }
+            if (inb) {
+                diag[t] = rdo;
+                if (t < nf) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j <= li) A[tri_off(t) + c0 + j] = v[j];
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) l11t[j * 16 + li] = (j <= li) ? v[j] : 0.0f;
+            }
+            if (lane == base) *flag = bad ? 1 : 0;
+        }
+        __syncthreads();
+        if (*flag) return false;
+        // rows below the block: L21 = A21 L_kk^-T, column by column
+        const bool below = li >= 16 && t < nf;
+        float a[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            a[c] = below ? v[c] * diag[c0 + c] : 0.0f;
+            const float4 *col = reinterpret_cast<const float4 *>(l11t + c * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (4 * q + 3 <= c) continue;
+                const float4 w = col[q];
+                if (4 * q > c) v[4 * q] = fmaf(-a[c], w.x, v[4 * q]);
+                if (4 * q + 1 > c) v[4 * q + 1] = fmaf(-a[c], w.y, v[4 * q + 1]);
+                if (4 * q + 2 > c) v[4 * q + 2] = fmaf(-a[c], w.z, v[4 * q + 2]);
+                v[4 * q + 3] = fmaf(-a[c], w.w, v[4 * q + 3]);
+            }
+        }
+        if (below) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c0 + c < nf) A[tri_off(t) + c0 + c] = a[c];
+        }
+        uint32_t hw[8], lw[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a[2 * i], a[2 * i + 1]);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(a[2 * i] - hf.x, a[2 * i + 1] - hf.y);
+            hw[i] = *reinterpret_cast<const uint32_t *>(&h);
+            lw[i] = *reinterpret_cast<const uint32_t *>(&l);
+        }
+        st_shared_v4(ops + rowoff, hw[0], hw[1], hw[2], hw[3]);
+        st_shared_v4(ops + rowoff + CH_LBO, hw[4], hw[5], hw[6], hw[7]);
+        st_shared_v4(ops + CH_TILE + rowoff, lw[0], lw[1], lw[2], lw[3]);
+        st_shared_v4(ops + CH_TILE + rowoff + CH_LBO, lw[4], lw[5], lw[6], lw[7]);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        const int ncol = ntc - c0 - 16;  // trailing columns (a multiple of 16)
+        if (ncol > 0 && t == 0 && !withhold) {
+            tc_fence_after();
+            const uint32_t id = idesc_bf16_f32_k_nega((uint32_t)ncol);
+            const uint32_t boff = (uint32_t)((c0 + 16) >> 3) * CH_SBO;
+            const uint64_t ah = smem_desc_noswz(ops, CH_LBO, CH_SBO);
+            const uint64_t al = smem_desc_noswz(ops + CH_TILE, CH_LBO, CH_SBO);
+            const uint64_t bh = smem_desc_noswz(ops + boff, CH_LBO, CH_SBO);
+            const uint64_t bl = smem_desc_noswz(ops + CH_TILE + boff, CH_LBO, CH_SBO);
+            const uint32_t dcol = tmem + (uint32_t)(c0 + 16);
+            tc_mma_bf16(dcol, ah, bh, id, 1u);
+            tc_mma_bf16(dcol, ah, bl, id, 1u);
+            tc_mma_bf16(dcol, al, bh, id, 1u);
+            tc_commit(mbar);
+        }
+    }
+    return true;
+}
+
 // resident CTAs per SM the register budget is set for
 __host__ __device__ constexpr int tc_min_blocks(int pfm, int kc) {
     return pfm == 2 ? (NSTG == 1 ? 4 : 3) : (pfm == 1 ? 4 : (kc == 16 ? 7 : 5));
@@ -122,7 +277,7 @@ __host__ __device__ constexpr int tc_min_blocks(int pfm, int kc) {
 
 template <int PFM, int KC>
 __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
-    k_sweep_tc(SweepArgs a, int ntc, const __grid_constant__ CUtensorMap tmap) {
+    k_sweep_tc(SweepArgs a, int ntc, int chol_tc, const __grid_constant__ CUtensorMap tmap) {
     constexpr bool PF = PFM == 1;
     constexpr bool TM = PFM == 2;
     constexpr int KCH = KC;
@@ -136,7 +291,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
     const uint32_t sbase = raw + pad;
     const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const TcLayout L = tc_layout(nf, a.ld, PFM, KC);
+    const TcLayout L = tc_layout(nf, a.ld, PFM, KC, chol_tc);
     float *A = reinterpret_cast<float *>(base + L.A);
     const float *stg = reinterpret_cast<const float *>(base + L.stg);
     float *vec = reinterpret_cast<float *>(base + L.vec);
@@ -266,11 +421,17 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                 bool swait = true;   // TMA: this chunk's rows arrived in time
                 const int sg = ch % NSTG;   // TMA: this chunk's staging tile
                 if constexpr (TM) tma_ids(ch + NSTG, ty);   // in flight while this chunk is split
-                if (pend[st]) {  // the MMAs of chunk ch-2 still read stage st
-                    const bool w = mbar_wait_bounded(mbar[st], phase[st], a.wait_ns);
-                    if (__syncthreads_or(!w)) { bail = true; break; }
-                    phase[st] ^= 1u;
-                    pend[st] = 0;
+                // the MMAs of chunk ch-2 read stage st: each thread waits for
+                // them before it writes its part of the stage (no CTA barrier
+                // here; a wait that ran out is noticed at the chunk's barrier
+                // and its thread writes nothing)
+                bool sok = true;
+                if (pend[st]) {
+                    sok = mbar_wait_bounded(mbar[st], phase[st], a.wait_ns);
+                    if (sok) {
+                        phase[st] ^= 1u;
+                        pend[st] = 0;
+                    }
                 }
                 int32_t cj[Q];
                 float cr[Q];
@@ -335,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
 #pragma unroll
                         for (int i = 0; i < 4; ++i) kadd(acc[i], cmp[i], cs[i]);
                     }
-                    if (act) {
+                    if (act && sok) {
                         const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
 #pragma unroll
                         for (int q = 0; q < Q; ++q) {
@@ -361,8 +522,8 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                 }
                 fence_proxy_async_smem();
                 // every thread has read staging tile st and written stage st;
-                // a TMA wait that ran out is noticed by all
-                if (__syncthreads_or(!swait)) { bail = true; break; }
+                // a wait that ran out is noticed by all
+                if (__syncthreads_or(!swait || !sok)) { bail = true; break; }
                 if (t == 0 && !a.withhold) {
                     tc_fence_after();
                     const uint32_t stage = sbase + L.ring + st * STAGE_BYTES;
@@ -411,8 +572,9 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
 #pragma unroll
             for (int i = 0; i < 4; ++i) part[warp * 128 + 4 * lane + i] = acc[i] - cmp[i];
             tc_fence_after();
-            // ---- 3. TMEM -> FP32 A (row m of D is TMEM lane m) -----------------
-            {
+            // TMEM -> FP32 A, D's lower triangle packed (row m of D is TMEM
+            // lane m), then TMEM is returned
+            auto read_out = [&]() {
                 const int m = 32 * warp + lane;
                 for (int c0 = 0; c0 < ntc; c0 += 16) {
                     float v[16];
@@ -425,14 +587,15 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                         }
                     }
                 }
-            }
-            tc_fence_before();
-            __syncthreads();
-            if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);  // read out: another CTA may take it
-            held = false;
+                tc_fence_before();
+                __syncthreads();
+                if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);  // read out: another CTA may take it
+                held = false;
+            };
             if (seg) {
-                // the slice's partials: D's lower triangle, packed as A is
-                // (row m at m (m + 1) / 2), then its residual at u0
+                // ---- 3. a slice of a split row: its Gram partial, packed as A
+                //      is, then its residual at u0 --------------------------------
+                read_out();
                 float *po = reinterpret_cast<float *>(a.seg_out) + r * a.seg_stride;
                 const int tri = nf * (nf + 1) / 2;
                 for (int e = t; e < tri; e += TC_THREADS) po[e] = A[e];
@@ -440,15 +603,37 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                 __syncthreads();
                 continue;
             }
-            // A = D + lambda n I (lower triangle); the first residual
-            // v1 = r0 - lambda n u0 (fixed order over the warps)
-            if (t < nf) {
-                A[tri_off(t) + t] += lam_n;
-                v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
+            if (chol_tc) {
+                // the first residual v1 = r0 - lambda n u0 (fixed order over
+                // the warps)
+                __syncthreads();
+                if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
+                // ---- 3-4. Cholesky of A = D + lambda n I from TMEM, trailing
+                //      updates on the tensor core --------------------------------
+                ok = chol_tmem(tmem, nf, ntc, lam_n, A, diag, work + 512, sbase + (uint32_t)L.ops, mbar[0],
+                               phase[0], a.wait_ns, a.withhold, t, bail);
+                if (bail) {
+                    // the last panel's MMAs may still write this CTA's TMEM
+                    if (t == 0 && !a.withhold) (void)mbar_wait_bounded(mbar[0], phase[0], a.wait_ns);
+                    __syncthreads();
+                    break;
+                }
+                tc_fence_before();
+                __syncthreads();
+                if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);  // factored: another CTA may take it
+                held = false;
+            } else {
+                // ---- 3. TMEM -> FP32 A; A = D + lambda n I, the first residual
+                //      v1 = r0 - lambda n u0 (fixed order over the warps) --------
+                read_out();
+                if (t < nf) {
+                    A[tri_off(t) + t] += lam_n;
+                    v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
+                }
+                __syncthreads();
+                // ---- 4. blocked Cholesky of A in shared memory ---------------
+                ok = chol_blocked128(A, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
             }
-            __syncthreads();
-            // ---- 4. Cholesky (inverted diagonal blocks), refinement ------------
-            ok = chol_blocked128(A, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
             if (ok) invert_diag_blocks128(A, nf, diag, t);
             if (!ok && t == 0) atomicAdd(a.notspd, 1);
         }
@@ -525,7 +710,7 @@ als_status fixed_side_map(const SweepArgs &a, CUtensorMap *m) {
 template <int PFM, int KC>
 als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     if (a.nrows <= 0) return ALS_OK;
-    const TcLayout L = tc_layout(a.nf, a.ld, PFM, KC);
+    const TcLayout L = tc_layout(a.nf, a.ld, PFM, KC, c->chol_tc);
     // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; cp.async
     // prefetching ~54 KB: 4; TMA-fed ~67 KB: 3
     size_t smem = (size_t)L.total + 1024;
@@ -550,7 +735,7 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     }
     cudaStream_t st = a.stream ? a.stream : c->stream;
     kt_begin(c, PFM ? KT_TC_PF : KT_TC, st);
-    k_sweep_tc<PFM, KC><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, tm);
+    k_sweep_tc<PFM, KC><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, c->chol_tc, tm);
     kt_end(c, PFM ? KT_TC_PF : KT_TC, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;

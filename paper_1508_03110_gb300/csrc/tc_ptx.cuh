@@ -68,6 +68,10 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
 // generic-proxy shared-memory writes -> visible to the async proxy (tensor core)
 // 16-byte asynchronous copy global -> shared (cached in L2 only), and its
 // group fences; a thread waits only for its own copies
@@ -106,6 +110,23 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo,
     d |= 1ull << 46;
     d |= 2ull << 61;
     return d;
+}
+// The same without swizzling (layout type 0): 8-row x 16-byte core matrices,
+// each 128 contiguous bytes; for K-major operands the leading byte offset is
+// the distance between core matrices adjacent in K, the stride byte offset
+// between core matrices adjacent in M/N.
+__device__ __forceinline__ uint64_t smem_desc_noswz(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, A
+// negated (bit 13), M = 128, N = n (multiple of 16, <= 256): D -= A B^T.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16_f32_k_nega(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both MN-major,
 // M = 128, N = n (multiple of 16, <= 256).
