@@ -595,14 +595,6 @@ def run_scale(args):
                       "lambda 0.05, mixed precision, FP32 factors, int32 indices", "results": results}), flush=True)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the sweep
-# kernels' launches from one ncu capture of this command's workload, summed
-# over one sweep's launches of that kernel, with the SHA-256 (first 16 hex
-# digits) of the kernel's sources when it was captured.  A figure is reported
-# only while those sources are unchanged.
-# Captured on a GB300 (profiles/sweep_dram_traffic_ml20m.md): the 4 launches
-# of k_sweep_tc in one sweep read 633.0 MB and wrote 15.3 MB; the 2 launches
-# of k_sweep_dual read 116.2 MB and wrote 35.5 MB.
 def tune_warm(m, x0, reps, warm=10):
     """Autotune at the state the timed iterations run in: `warm` ALS-NCG
     iterations from x0 first (untimed setup), so that the trial sweeps see
@@ -616,7 +608,14 @@ def tune_warm(m, x0, reps, warm=10):
     return tune
 
 
-TRAFFIC = {"k_sweep_tc": ("1beaf3dee73b068b", 648311040), "k_sweep_dual": ("91b1801e7dcbadbf", 151659264)}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the sweep
+# kernels' launches from one ncu capture of this command's workload, summed
+# over one sweep's launches of that kernel, with the SHA-256 (first 16 hex
+# digits) of the kernel's sources and the launch shapes of the capture.  A
+# figure is reported only while those sources are unchanged and the bench
+# runs with the same shapes (the autotuner's choice; another choice gives
+# other launches).
+TRAFFIC = {}
 TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh"),
                    "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh")}
 
@@ -630,13 +629,17 @@ def kernel_source_sha(name):
     return h.hexdigest()[:16]
 
 
-def traffic_for(name, launches):
+def shapes_key(launch):
+    return ",".join(f"{k}={launch[k]}" for k in sorted(launch))
+
+
+def traffic_for(name, launches, launch):
     """DRAM bytes per launch of `name` (its captured per-sweep total over its
-    launches), or None if not captured for the current sources."""
+    launches), or None if not captured for the current sources and shapes."""
     t = TRAFFIC.get(name)
-    if not t or t[0] != kernel_source_sha(name) or launches < 1:
+    if not t or t[0] != kernel_source_sha(name) or t[1] != shapes_key(launch) or launches < 1:
         return None
-    return t[1] / launches
+    return t[2] / launches
 
 
 def load_peaks():
@@ -896,20 +899,23 @@ def main():
     nf, ld = r.n_f, (r.n_f + 3) // 4 * 4
     fl, gram = sweep_flops(r, r.n_f, args.refine, args.precision, launch.get("dual_max", 0) if use_tc else 0)
     kernels = {}
-    for name in ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split"):
+    for name in ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split", "k_sweep_tc_seg"):
         k = ts[name]
         if k["launches"]:
             kernels[name] = {"ms_per_sweep": k["ms"], "launches_per_sweep": k["launches"], "rows": k["rows"],
                              "ratings": k["ratings"], "share_of_sweep": k["ms"] / ts["sweep_ms"]}
     if use_tc:
-        # k_sweep_tc (both variants): the dense contraction is the symmetric
-        # Gram, n_f (n_f + 1) flop per rating of its rows; its Cholesky,
-        # solves and residuals run on the FP32 ALU; its gather reads one FP32
-        # factor row (4 ld bytes) plus 8 bytes of id and value per rating
-        k_ms = ts["k_sweep_tc_pf"]["ms"] + ts["k_sweep_tc"]["ms"]
-        k_ratings = ts["k_sweep_tc_pf"]["ratings"] + ts["k_sweep_tc"]["ratings"]
+        # k_sweep_tc (all its launches: both whole-row variants and the split
+        # rows' segments): the dense contraction is the symmetric Gram,
+        # n_f (n_f + 1) flop per rating of its rows; the whole rows' Cholesky,
+        # solves and residuals run on the FP32 ALU (a split row is factored by
+        # k_split_solve); its gather reads one FP32 factor row (4 ld bytes)
+        # plus 8 bytes of id and value per rating
+        tcs = ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_tc_seg")
+        k_ms = sum(ts[n]["ms"] for n in tcs)
+        k_ratings = sum(ts[n]["ratings"] for n in tcs)
         k_rows = ts["k_sweep_tc_pf"]["rows"] + ts["k_sweep_tc"]["rows"]
-        k_launches = ts["k_sweep_tc_pf"]["launches"] + ts["k_sweep_tc"]["launches"]
+        k_launches = sum(ts[n]["launches"] for n in tcs)
         gram_k = float(k_ratings) * nf * (nf + 1)
         alu_k = float(k_rows) * (nf ** 3 / 3.0 + args.refine * 2 * nf ** 2) + \
             float(k_ratings) * args.refine * 4 * nf
@@ -924,11 +930,12 @@ def main():
         gather = {"achieved_gbs": float(k_ratings) * (4 * ld + 8) / (k_ms / 1e3) / 1e9,
                   "what": "gathered factor rows + ids/values per rating (mostly L2 hits: the fixed side "
                           "is 10.7 MB (M) or 55 MB (U))"}
-        kname = "k_sweep_tc (both variants: rows of >= 256 ratings prefetch their factor rows)"
+        kname = ("k_sweep_tc (all launches: rows of >= 256 ratings prefetch their factor rows; the split "
+                 "rows' segments)")
         per_launch_ms = k_ms / max(1, k_launches)
         work = {"gram_flop_per_launch": gram_k / max(1, k_launches), "ratings": k_ratings, "rows": k_rows,
                 "launches_per_sweep": k_launches, "ms_per_launch": per_launch_ms}
-        traffic = traffic_for("k_sweep_tc", k_launches)
+        traffic = traffic_for("k_sweep_tc", k_launches, launch)
     else:
         alu_part, gather = None, None
         k_ms = ts["k_sweep_fma"]["ms"]

@@ -489,16 +489,19 @@ ALS_API als_status als_rank_accuracy(als_ctx *ctx, int32_t t, const int32_t *top
  *   1 k_sweep_tc, the other tensor-core rows
  *   2 k_sweep_dual, the light rows (solved through their n_i x n_i matrix)
  *   3 k_sweep_fma (FP64 form, or FP32 Gram for small n_f)
- *   4 the split heavy rows (segment partials, sums, solves; side stream)
+ *   4 the split heavy rows (segment partials, sums, solves)
+ *   5 k_sweep_tc in segment mode: the split rows' partials (part of 4)
  * Per class: the summed launch durations per sweep (ms), the launches, rows
  * and ratings one sweep gives it (both halves).  sweep_ms: the whole sweep,
- * events on the context's stream.  Synchronous. */
+ * events on the context's stream.  While timing, the split part runs on the
+ * context's stream rather than beside the other rows, so that every launch
+ * is timed alone.  Synchronous. */
 typedef struct {
     double sweep_ms;
-    double ms[5];
-    int64_t rows[5];
-    int64_t ratings[5];
-    int32_t launches[5];
+    double ms[6];
+    int64_t rows[6];
+    int64_t ratings[6];
+    int32_t launches[6];
 } als_sweep_timing;
 ALS_API als_status als_time_sweep(als_ctx *ctx, int32_t reps, als_sweep_timing *out);
 

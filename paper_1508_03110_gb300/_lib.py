@@ -72,12 +72,12 @@ class ServerConfig(ctypes.Structure):
 
 class SweepTiming(ctypes.Structure):
     _fields_ = [
-        ("sweep_ms", ctypes.c_double), ("ms", ctypes.c_double * 5), ("rows", ctypes.c_int64 * 5),
-        ("ratings", ctypes.c_int64 * 5), ("launches", ctypes.c_int32 * 5),
+        ("sweep_ms", ctypes.c_double), ("ms", ctypes.c_double * 6), ("rows", ctypes.c_int64 * 6),
+        ("ratings", ctypes.c_int64 * 6), ("launches", ctypes.c_int32 * 6),
     ]
 
 
-SWEEP_CLASSES = ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split")
+SWEEP_CLASSES = ("k_sweep_tc_pf", "k_sweep_tc", "k_sweep_dual", "k_sweep_fma", "split", "k_sweep_tc_seg")
 
 # name -> (restype, argtypes); the full list of symbols include/als.h declares
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double

@@ -134,6 +134,16 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.dual_nmax = std::min(c->dual_max, c->nf);
     const int64_t H = c->nsplit[side];
     if (H == 0) return launch_sweep(c, a, c->f64, c->use_tc);
+    if (c->kt && c->kt->serial) {
+        // per-kernel timing: every launch on the context's stream, so that
+        // each one's events time it alone
+        als_status s = launch_split_sweep(c, a, side);
+        if (s != ALS_OK) return s;
+        a.order += H;
+        a.nrows -= H;
+        a.nbig = std::max<int64_t>(0, a.nbig - H);
+        return launch_sweep(c, a, c->f64, c->use_tc);
+    }
     // the heaviest rows, split across CTAs, on the side stream; the rest, one
     // CTA (or warp) each, beside them on the context's stream (inside a
     // captured iteration the two become parallel branches of the graph)
@@ -1402,13 +1412,13 @@ extern "C" als_status als_selftest_wait_expiry(als_ctx *c, double limit_s, int64
 
 void kt_begin(als_ctx *c, int cls, cudaStream_t st) {
     KTimer *k = c->kt;
-    if (!k || k->depth > 0 || k->n[cls] >= KTimer::kMax) return;
+    if (!k || (k->depth > 0 && cls != KT_TC_SEG) || k->n[cls] >= KTimer::kMax) return;
     cudaEventRecord(k->ev[cls][k->n[cls]][0], st);
 }
 
 void kt_end(als_ctx *c, int cls, cudaStream_t st) {
     KTimer *k = c->kt;
-    if (!k || k->depth > 0 || k->n[cls] >= KTimer::kMax) return;
+    if (!k || (k->depth > 0 && cls != KT_TC_SEG) || k->n[cls] >= KTimer::kMax) return;
     cudaEventRecord(k->ev[cls][k->n[cls]][1], st);
     k->n[cls] += 1;
 }
@@ -1436,6 +1446,7 @@ extern "C" als_status als_time_sweep(als_ctx *c, int32_t reps, als_sweep_timing 
             for (int64_t r = b; r < e; ++r) out->ratings[cls] += d[r];
         };
         add(KT_SPLIT, 0, H);
+        if (tc) add(KT_TC_SEG, 0, H);
         if (tc) {
             const int64_t npf = std::min(c->sweep_pf[side], n - H);
             const int64_t nd = std::min(c->sweep_dual[side], n - H);
@@ -1448,6 +1459,7 @@ extern "C" als_status als_time_sweep(als_ctx *c, int32_t reps, als_sweep_timing 
     }
     KTimer kt;
     std::memset(&kt, 0, sizeof kt);
+    kt.serial = true;
     for (int a = 0; a < KT_NCLASS; ++a)
         for (int i = 0; i < KTimer::kMax; ++i)
             for (int j = 0; j < 2; ++j)

@@ -51,12 +51,14 @@ struct LsParams {
 // holds a KTimer, each sweep launch records a CUDA event pair on the stream
 // it is launched on.  Classes: 0 k_sweep_tc prefetching variant, 1 k_sweep_tc,
 // 2 k_sweep_dual, 3 k_sweep_fma, 4 the split heavy rows (all their launches).
-enum { KT_TC_PF = 0, KT_TC = 1, KT_DUAL = 2, KT_FMA = 3, KT_SPLIT = 4, KT_NCLASS = 5 };
+enum { KT_TC_PF = 0, KT_TC = 1, KT_DUAL = 2, KT_FMA = 3, KT_SPLIT = 4, KT_TC_SEG = 5, KT_NCLASS = 6 };
 struct KTimer {
     static constexpr int kMax = 16;          // launches per class between two reads
     cudaEvent_t ev[KT_NCLASS][kMax][2];
     int n[KT_NCLASS];
     int depth;                               // > 0 inside the split part: its own launches
+                                             // (but for KT_TC_SEG, the tensor-core segment launches)
+    bool serial;                             // the split part runs on the context's stream
 };
 void kt_begin(struct als_ctx *c, int cls, cudaStream_t st);
 void kt_end(struct als_ctx *c, int cls, cudaStream_t st);

@@ -734,9 +734,10 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
         return ALS_ENOTSUP;
     }
     cudaStream_t st = a.stream ? a.stream : c->stream;
-    kt_begin(c, PFM ? KT_TC_PF : KT_TC, st);
+    const int cls = a.seg_out ? KT_TC_SEG : (PFM ? KT_TC_PF : KT_TC);
+    kt_begin(c, cls, st);
     k_sweep_tc<PFM, KC><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, c->chol_tc, tm);
-    kt_end(c, PFM ? KT_TC_PF : KT_TC, st);
+    kt_end(c, cls, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
 }
