@@ -397,6 +397,9 @@ ALS_API void als_server_destroy(als_server *srv);
  *                  memory on the CUDA cores (0), or in place in TMEM by
  *                  panels of 16 columns whose trailing updates are tcgen05
  *                  MMAs (1)
+ *   dual_warp      light rows of at most 32 ratings: a CTA per row (0), or a
+ *                  warp per row, G's Cholesky factor a row per lane in
+ *                  registers (1)
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t heavy_min;        /* default 512    */
@@ -409,6 +412,7 @@ typedef struct {
     int32_t gather_tma;       /* default 0      */
     int32_t tc_chunk;         /* default 32     */
     int32_t chol_tc;          /* default 0      */
+    int32_t dual_warp;        /* default 1      */
 } als_launch;
 
 ALS_API als_status als_get_launch(als_ctx *ctx, als_launch *out);

@@ -51,7 +51,7 @@ class Launch(ctypes.Structure):
         ("heavy_min", ctypes.c_int32), ("grid_mult", ctypes.c_int32), ("sweep_bin_min", ctypes.c_int32),
         ("split_min", ctypes.c_int32), ("seg_len", ctypes.c_int32), ("gram_path", ctypes.c_int32),
         ("dual_max", ctypes.c_int32), ("gather_tma", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
-        ("chol_tc", ctypes.c_int32),
+        ("chol_tc", ctypes.c_int32), ("dual_warp", ctypes.c_int32),
     ]
 
 

@@ -1123,6 +1123,7 @@ void fill_launch(const als_ctx *c, als_launch *o) {
     o->gather_tma = c->gather_tma;
     o->tc_chunk = c->tc_chunk16 ? 16 : 32;
     o->chol_tc = c->chol_tc;
+    o->dual_warp = c->dual_warp;
 }
 
 // apply launch shapes (validated by the caller); rebuilds what depends on them
@@ -1148,6 +1149,7 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
     c->gather_tma = l.gather_tma;
     c->tc_chunk16 = l.tc_chunk == 16;
     c->chol_tc = l.chol_tc;
+    c->dual_warp = l.dual_warp;
     count_sweep_rows(c);
     destroy_graphs(c);  // the captured iterations hold the old launch shapes
     return ALS_OK;
@@ -1156,7 +1158,8 @@ als_status apply_launch(als_ctx *c, const als_launch &l) {
 bool launch_valid(const als_ctx *c, const als_launch &l) {
     if (l.heavy_min < 1 || l.grid_mult < 1 || l.grid_mult > 64 || l.sweep_bin_min < 0 || l.split_min < 0 ||
         l.seg_len < 32 || l.dual_max < 0 || l.dual_max > ALS_DUAL_MAX || l.gather_tma < 0 || l.gather_tma > 1 ||
-        (l.tc_chunk != 16 && l.tc_chunk != 32) || l.chol_tc < 0 || l.chol_tc > 1)
+        (l.tc_chunk != 16 && l.tc_chunk != 32) || l.chol_tc < 0 || l.chol_tc > 1 ||
+        l.dual_warp < 0 || l.dual_warp > 1)
         return false;
     if (l.gram_path != ALS_GRAM_FMA && l.gram_path != ALS_GRAM_TC) return false;
     if (l.gram_path == ALS_GRAM_TC && (c->f64 || c->nf > ALS_TC_LD)) return false;
@@ -1175,7 +1178,7 @@ extern "C" als_status als_set_launch(als_ctx *c, const als_launch *in) {
     if (!c || !in || !launch_valid(c, *in)) {
         als_set_error("als_set_launch: bad argument (heavy_min >= 1, grid_mult 1..64, sweep_bin_min >= 0, "
                       "split_min >= 0, seg_len >= 32, gram_path FMA, or TC for the mixed form, dual_max 0..64, "
-                      "gather_tma 0 or 1, tc_chunk 16 or 32, chol_tc 0 or 1)");
+                      "gather_tma 0 or 1, tc_chunk 16 or 32, chol_tc 0 or 1, dual_warp 0 or 1)");
         return ALS_EINVAL;
     }
     return apply_launch(c, *in);
@@ -1275,6 +1278,12 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
         for (int d : {0, 16, 32, 48, 64}) {
             als_launch cand = cur;
             cand.dual_max = d;
+            if ((s = trial(cand, false, best)) != ALS_OK) return s;
+        }
+        // the light rows of <= 32 ratings: a CTA or a warp each
+        for (int w : {0, 1}) {
+            als_launch cand = cur;
+            cand.dual_warp = w;
             if ((s = trial(cand, false, best)) != ALS_OK) return s;
         }
     }

@@ -109,3 +109,23 @@ def test_chol_tc_fullsize_matches_shared_memory_cholesky():
             fs[ct] = np.array([i["f"] for i in infos])
             assert infos[-1]["notspd"] == 0
     assert np.all(np.abs(fs[1] - fs[0]) <= 1e-6 * np.abs(fs[0]))
+
+
+def test_chol_tc_foldin_matches_the_oracle(tiny):
+    """Fold-in requests (1..800 ratings, cold start u0 = 0) with the TMEM
+    factorisation and five corrections: every answer within 1e-6 of the
+    oracle's exact solve."""
+    from test_gpu_parity import _kappas
+    r = tiny
+    n_f = 100
+    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 3).astype(np.float32).astype(np.float64)
+    ptr, items, vals = synth.foldin_requests(30, r.n_m, 1, 800, seed=9)
+    ref = oracle.foldin(n_f, r.lam, x0[r.n_u * n_f:], ptr, items, vals.astype(np.float64))
+    with _als(r, n_f, refine_steps=5) as m:
+        m.set_launch(chol_tc=1, dual_max=0)
+        m.set_x(x0)
+        u = m.foldin(ptr, items, vals)
+    Mf = x0[r.n_u * n_f:].reshape(r.n_m, n_f)
+    kap = _kappas(ptr, items, Mf, r.lam, np.arange(len(ptr) - 1))
+    assert _mixed_row_excess(u, ref, np.zeros_like(ref), kap, 1e-6) < 1.0
+    assert _row_rel(u, ref, n_f) < 1e-6

@@ -1,7 +1,9 @@
 """Light-row solve of the mixed tensor-core sweep: rows of at most
 min(dual_max, n_f) ratings are solved through F F^T + lambda n_i I (Woodbury
 identity) instead of the n_f x n_f matrix of Eq. (3) / (4).  Same rows as the
-FP64 oracle's solve, same ALS-NCG trajectory as the FP64 run (needs a GB300)."""
+FP64 oracle's solve, same ALS-NCG trajectory as the FP64 run (needs a GB300);
+with a CTA per row, and (dual_warp) with a warp per row of at most 32
+ratings."""
 import numpy as np
 import pytest
 
@@ -39,9 +41,10 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
+@pytest.mark.parametrize("dual_warp", [0, 1])
 @pytest.mark.parametrize("n_f", [36, 50, 98, 100, 128])
-@pytest.mark.parametrize("dual_max", [0, 16, 64])
-def test_dual_sweep_matches_oracle(n_f, dual_max):
+@pytest.mark.parametrize("dual_max", [0, 16, 32, 64])
+def test_dual_sweep_matches_oracle(n_f, dual_max, dual_warp):
     """One sweep with enough refinement steps: every user row (solved from the
     same item rows as the oracle's) within 1e-5 of the oracle's row, the whole
     x within 1e-5."""
@@ -50,8 +53,8 @@ def test_dual_sweep_matches_oracle(n_f, dual_max):
     x0 = synth.init_factors(n_u, n_m, n_f, 5)
     ref = oracle.sweep(P, x0)
     with _model(n_u, n_m, rows, cols, vals, n_f, precision="mixed", gram_path="tc", refine_steps=4) as m:
-        m.set_launch(dual_max=dual_max)
-        assert m.get_launch()["dual_max"] == dual_max
+        m.set_launch(dual_max=dual_max, dual_warp=dual_warp)
+        assert m.get_launch()["dual_max"] == dual_max and m.get_launch()["dual_warp"] == dual_warp
         m.set_x(x0)
         m.sweep(1)
         x = m.get_x()
@@ -64,7 +67,8 @@ def test_dual_sweep_matches_oracle(n_f, dual_max):
     assert _rel(x, ref) < 1e-5
 
 
-def test_dual_single_correction_is_accurate():
+@pytest.mark.parametrize("dual_warp", [0, 1])
+def test_dual_single_correction_is_accurate(dual_warp):
     """From a random start one correction through G leaves an error of order
     kappa(A) times FP32 rounding on the light rows, far below the tensor-core
     Gram's (BF16 split) first correction."""
@@ -76,7 +80,7 @@ def test_dual_single_correction_is_accurate():
     deg = np.bincount(rows, minlength=n_u)
     light = (deg > 0) & (deg <= 64)
     with _model(n_u, n_m, rows, cols, vals, n_f, precision="mixed", gram_path="tc", refine_steps=1) as m:
-        m.set_launch(dual_max=64)
+        m.set_launch(dual_max=64, dual_warp=dual_warp)
         m.set_x(x0)
         m.sweep(1)
         x = m.get_x()
@@ -85,8 +89,8 @@ def test_dual_single_correction_is_accurate():
     assert np.max(err) < 1e-4, np.max(err)
 
 
-@pytest.mark.parametrize("dual_max", [16, 64])
-def test_dual_alsncg_matches_fp64_run(dual_max):
+@pytest.mark.parametrize("dual_max,dual_warp", [(16, 0), (64, 0), (64, 1)])
+def test_dual_alsncg_matches_fp64_run(dual_max, dual_warp):
     """ALS-NCG with the light-row solve: f within 1e-5 of the FP64 run at equal
     iteration count, no row left unsolved."""
     n_u, n_m, rows, cols, vals = _dual_problem(copies=10, seed=1)
@@ -96,7 +100,7 @@ def test_dual_alsncg_matches_fp64_run(dual_max):
     for prec in ("fp64", "mixed"):
         with _model(n_u, n_m, rows, cols, vals, n_f, precision=prec) as m:
             if prec == "mixed":
-                m.set_launch(dual_max=dual_max)
+                m.set_launch(dual_max=dual_max, dual_warp=dual_warp)
             m.set_x(x0)
             fs[prec] = np.array([m.step()["f"] for _ in range(25)])
             out = m.run(1)
@@ -113,13 +117,14 @@ def test_dual_tiny_workload_trajectory():
     n_f = 100
     x0 = synth.init_factors(r.n_u, r.n_m, n_f, 9)
     fs = {}
-    for key, prec, d in (("fp64", "fp64", 0), ("dual", "mixed", 64), ("tc", "mixed", 0)):
+    for key, prec, d, w in (("fp64", "fp64", 0, 0), ("dual", "mixed", 64, 0), ("warp", "mixed", 64, 1),
+                            ("tc", "mixed", 0, 0)):
         with _model(r.n_u, r.n_m, r.rows, r.cols, r.vals, n_f, precision=prec) as m:
             if prec == "mixed":
-                m.set_launch(dual_max=d)
+                m.set_launch(dual_max=d, dual_warp=w)
             m.set_x(x0)
             fs[key] = np.array([m.step()["f"] for _ in range(20)])
-    for key in ("dual", "tc"):
+    for key in ("dual", "warp", "tc"):
         assert np.all(np.abs(fs[key] - fs["fp64"]) <= 1e-5 * np.abs(fs["fp64"])), key
 
 
@@ -131,3 +136,29 @@ def test_dual_bound_rejected_out_of_range():
             m.set_launch(dual_max=65)
         with pytest.raises(ALSError, match="EINVAL"):
             m.set_launch(dual_max=-1)
+
+
+def test_dual_warp_foldin_matches_oracle():
+    """Fold-in requests of 1..40 ratings against fixed item rows (a cold
+    start, u0 = 0) with a warp per request of at most 32 ratings: every answer
+    within 1e-5 of the oracle's exact solve."""
+    n_u, n_m, rows, cols, vals = _dual_problem(copies=2, seed=5)
+    n_f = 100
+    x0 = synth.init_factors(n_u, n_m, n_f, 6).astype(np.float32).astype(np.float64)
+    ptr, items, rv = synth.foldin_requests(48, n_m, 1, 40, seed=12)
+    ref = oracle.foldin(n_f, 0.05, x0[n_u * n_f:], ptr, items, rv.astype(np.float64))
+    with _model(n_u, n_m, rows, cols, vals, n_f, precision="mixed", gram_path="tc", refine_steps=4) as m:
+        m.set_launch(dual_max=64, dual_warp=1)
+        m.set_x(x0)
+        u = m.foldin(ptr, items, rv).reshape(-1, n_f)
+    ref = ref.reshape(-1, n_f)
+    err = np.linalg.norm(u - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-30)
+    assert np.max(err) < 1e-5, np.max(err)
+
+
+def test_dual_warp_rejected_out_of_range():
+    from paper_1508_03110_gb300 import ALSError
+    n_u, n_m, rows, cols, vals = _dual_problem(copies=1)
+    with _model(n_u, n_m, rows, cols, vals, 100, precision="mixed") as m:
+        with pytest.raises(ALSError, match="EINVAL"):
+            m.set_launch(dual_warp=2)
