@@ -440,8 +440,9 @@ ALS_API als_status als_autotune(als_ctx *ctx, int32_t reps, als_tune_report *out
 /* Groups: run max_iter ALS-NCG iterations (Algorithm 2) of n distinct
  * contexts together, e.g. one batched context per n_f of a mixed collection of
  * problems.  Each iteration launches every member's captured iteration on the
- * member's own stream (members must use distinct streams), so the members'
- * kernels overlap on the GPU.  Every check_every iterations the relative
+ * member's stream: members that share a stream run one after another, members
+ * on distinct streams may overlap on the GPU (members must be distinct
+ * contexts).  Every check_every iterations the relative
  * gradient norms are read; the run stops once every problem of every member
  * has |g_k| <= rel_tol |g_0| (rel_tol = 0: never).  last (may be NULL): n
  * records, one per member, as alsncg_run's; *iters_done: iterations run. */

@@ -527,18 +527,23 @@ class Server:
 
 class ALSGroup:
     """A collection of independent problems with different n_f: one batched
-    context per n_f value (all its problems in the same launches), each on
-    its own CUDA stream, iterated together by als_group_run so that the
-    contexts' kernels overlap on the GPU.
+    context per n_f value (all its problems in the same launches), iterated
+    together by als_group_run.
 
     problems: list of (n_u, n_m, rows, cols, vals) with local ids; n_fs: the
     n_f of each problem."""
 
-    def __init__(self, problems, n_fs, lam, precision="mixed", autotune=True, priorities=True, **kw):
-        """priorities: the member with the most work per iteration (ratings x
-        n_f^2) gets the highest stream priority, the next one the next, so the
-        dominant context's CTAs are dispatched first and the others fill the
-        SMs it leaves idle."""
+    def __init__(self, problems, n_fs, lam, precision="mixed", autotune=True, priorities=True,
+                 schedule="concurrent", **kw):
+        """schedule: "serial" puts every member on one stream, so that each
+        iteration runs the members' graphs one after another (each one's
+        launches fill the GPU by themselves); "concurrent" gives each member a
+        stream of its own, so that their kernels may overlap.  priorities
+        (concurrent only): the member with the most work per iteration
+        (ratings x n_f^2) gets the highest stream priority, the next one the
+        next."""
+        if schedule not in ("serial", "concurrent"):
+            raise ValueError("schedule: 'serial' or 'concurrent'")
         torch = _torch()
         self.lib = _lib.load()
         self.order = {}
@@ -547,13 +552,18 @@ class ALSGroup:
         self.n_prob = len(problems)
         work = {nf: sum(len(problems[q][4]) for q in qs) * nf * nf for nf, qs in self.order.items()}
         ranked = sorted(self.order, key=lambda nf: -work[nf])
-        if priorities:
-            least, greatest = torch.cuda.Stream.priority_range()
-            span = list(range(greatest, least + 1)) if greatest <= least else list(range(greatest, least - 1, -1))
-            prio = {nf: span[min(i, len(span) - 1)] for i, nf in enumerate(ranked)}
+        if schedule == "serial":
+            one = torch.cuda.Stream()
+            self.streams = {nf: one for nf in self.order}
         else:
-            prio = {nf: 0 for nf in ranked}
-        self.streams = {nf: torch.cuda.Stream(priority=prio[nf]) for nf in self.order}
+            if priorities:
+                least, greatest = torch.cuda.Stream.priority_range()
+                span = (list(range(greatest, least + 1)) if greatest <= least
+                        else list(range(greatest, least - 1, -1)))
+                prio = {nf: span[min(i, len(span) - 1)] for i, nf in enumerate(ranked)}
+            else:
+                prio = {nf: 0 for nf in ranked}
+            self.streams = {nf: torch.cuda.Stream(priority=prio[nf]) for nf in self.order}
         self.batches = {nf: ALSBatch([problems[q] for q in qs], nf, lam, precision=precision,
                                      stream=self.streams[nf], **kw)
                         for nf, qs in self.order.items()}

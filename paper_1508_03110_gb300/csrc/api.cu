@@ -1315,8 +1315,8 @@ extern "C" als_status als_group_run(als_ctx **ctxs, int32_t n, int32_t max_iter,
     for (int32_t i = 0; i < n; ++i) {
         if (!ctxs[i]) { als_set_error("als_group_run: a member is NULL"); return ALS_EINVAL; }
         for (int32_t j = 0; j < i; ++j) {
-            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) {
-                als_set_error("als_group_run: members must be distinct contexts on distinct streams");
+            if (ctxs[j] == ctxs[i]) {
+                als_set_error("als_group_run: members must be distinct contexts");
                 return ALS_EINVAL;
             }
         }

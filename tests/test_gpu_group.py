@@ -34,11 +34,18 @@ def test_group_fp64_matches_oracle_per_problem(probs):
         assert _rel(got[q], refs[q][-1].x) < 1e-9, q
 
 
-def test_group_equals_members_alone(probs):
+@pytest.mark.parametrize("schedule", ["serial", "concurrent"])
+def test_group_equals_members_alone(probs, schedule):
+    """One stream for all members or one each: the same factors, bit for bit,
+    as each member run on its own."""
     from paper_1508_03110_gb300 import ALSGroup
     n_fs = [10, 20, 50, 100] * 2
     xs = [synth.init_factors(nu, nm, nf, 60 + q) for q, ((nu, nm, *_r), nf) in enumerate(zip(probs, n_fs))]
-    with ALSGroup(probs, n_fs, 0.05, precision="mixed", autotune=False) as g:
+    with ALSGroup(probs, n_fs, 0.05, precision="mixed", autotune=False, schedule=schedule) as g:
+        if schedule == "serial":
+            assert len({id(st) for st in g.streams.values()}) == 1
+        else:
+            assert len({id(st) for st in g.streams.values()}) == len(g.streams)
         g.set_x(xs)
         g.run(12, check_every=4)
         together = g.get_x()
@@ -51,7 +58,7 @@ def test_group_equals_members_alone(probs):
         assert np.array_equal(together[q], alone[q]), q
 
 
-def test_group_converges_and_rejects_shared_streams(probs):
+def test_group_converges_and_rejects_a_repeated_member(probs):
     import ctypes
     from paper_1508_03110_gb300 import ALSError, ALSGroup, _lib
     n_fs = [10, 20, 50, 100] * 2
