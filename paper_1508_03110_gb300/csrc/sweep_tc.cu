@@ -275,9 +275,11 @@ __host__ __device__ constexpr int tc_min_blocks(int pfm, int kc) {
     return pfm == 2 ? (NSTG == 1 ? 4 : 3) : (pfm == 1 ? 4 : (kc == 16 ? 7 : 5));
 }
 
-template <int PFM, int KC>
+// CT: the factorisation in TMEM (launch shape chol_tc); a template parameter
+// so that each kernel carries only the code of its own factorisation
+template <int PFM, int KC, int CT>
 __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
-    k_sweep_tc(SweepArgs a, int ntc, int chol_tc, const __grid_constant__ CUtensorMap tmap) {
+    k_sweep_tc(SweepArgs a, int ntc, const __grid_constant__ CUtensorMap tmap) {
     constexpr bool PF = PFM == 1;
     constexpr bool TM = PFM == 2;
     constexpr int KCH = KC;
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
     const uint32_t sbase = raw + pad;
     const int nf = a.nf;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const TcLayout L = tc_layout(nf, a.ld, PFM, KC, chol_tc);
+    const TcLayout L = tc_layout(nf, a.ld, PFM, KC, CT);
     float *A = reinterpret_cast<float *>(base + L.A);
     const float *stg = reinterpret_cast<const float *>(base + L.stg);
     float *vec = reinterpret_cast<float *>(base + L.vec);
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                 __syncthreads();
                 continue;
             }
-            if (chol_tc) {
+            if constexpr (CT) {
                 // the first residual v1 = r0 - lambda n u0 (fixed order over
                 // the warps)
                 __syncthreads();
@@ -707,16 +709,16 @@ als_status fixed_side_map(const SweepArgs &a, CUtensorMap *m) {
     return ALS_OK;
 }
 
-template <int PFM, int KC>
-als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
+template <int PFM, int KC, int CT>
+als_status launch_tc_ct(als_ctx *c, const SweepArgs &a, int ntc) {
     if (a.nrows <= 0) return ALS_OK;
-    const TcLayout L = tc_layout(a.nf, a.ld, PFM, KC, c->chol_tc);
+    const TcLayout L = tc_layout(a.nf, a.ld, PFM, KC, CT);
     // ~40 KB of shared memory per CTA (n_f = 100): 5 CTAs per SM; cp.async
     // prefetching ~54 KB: 4; TMA-fed ~67 KB: 3
     size_t smem = (size_t)L.total + 1024;
-    if (raise_smem_limit((const void *)k_sweep_tc<PFM, KC>, smem) != ALS_OK) return ALS_ECUDA;
+    if (raise_smem_limit((const void *)k_sweep_tc<PFM, KC, CT>, smem) != ALS_OK) return ALS_ECUDA;
     // the whole L1/shared array as shared memory, so that 5-7 CTAs fit per SM
-    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PFM, KC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    ALS_CUDA_TRY(cudaFuncSetAttribute(k_sweep_tc<PFM, KC, CT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     CUtensorMap tm;
     std::memset(&tm, 0, sizeof tm);
@@ -736,10 +738,16 @@ als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
     cudaStream_t st = a.stream ? a.stream : c->stream;
     const int cls = a.seg_out ? KT_TC_SEG : (PFM ? KT_TC_PF : KT_TC);
     kt_begin(c, cls, st);
-    k_sweep_tc<PFM, KC><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, c->chol_tc, tm);
+    k_sweep_tc<PFM, KC, CT><<<(unsigned)a.nrows, TC_THREADS, smem, st>>>(a, ntc, tm);
     kt_end(c, cls, st);
     ALS_CUDA_TRY(cudaGetLastError());
     return ALS_OK;
+}
+
+// segments factor nothing: always the kernel without the TMEM factorisation
+template <int PFM, int KC>
+als_status launch_tc(als_ctx *c, const SweepArgs &a, int ntc) {
+    return (c->chol_tc && !a.seg_out) ? launch_tc_ct<PFM, KC, 1>(c, a, ntc) : launch_tc_ct<PFM, KC, 0>(c, a, ntc);
 }
 
 }  // namespace
