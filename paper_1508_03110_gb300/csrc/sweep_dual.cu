@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(DU_THREADS, MINB) k_sweep_dual(SweepArgs a, in
 
 }  // namespace
 
-als_status launch_sweep_dual_warp(als_ctx *c, const SweepArgs &a);  // sweep_dual_warp.cu
+als_status launch_sweep_dual_warp(als_ctx *c, const SweepArgs &a, int nmax);  // sweep_dual_warp.cu
 
 namespace {
 
@@ -313,7 +313,7 @@ als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
         als_set_error("sweep: more rows than CTAs in one launch");
         return ALS_ENOTSUP;
     }
-    if (nmax <= ALS_DUAL_SMALL) return c->dual_warp ? launch_sweep_dual_warp(c, a) : launch_dual<7>(c, a, nmax);
+    if (nmax <= ALS_DUAL_SMALL) return c->dual_warp ? launch_sweep_dual_warp(c, a, nmax) : launch_dual<7>(c, a, nmax);
     // the rows (a suffix of the degree order) of at most ALS_DUAL_SMALL
     // ratings in the smaller layout, the longer ones before them
     const int64_t ns = a.order ? std::max<int64_t>(0, std::min(a.ndual_small, a.nrows)) : 0;
@@ -327,5 +327,5 @@ als_status launch_sweep_dual(als_ctx *c, const SweepArgs &a, int nmax) {
     SweepArgs sm = a;
     sm.order = a.order + (a.nrows - ns);
     sm.nrows = ns;
-    return c->dual_warp ? launch_sweep_dual_warp(c, sm) : launch_dual<7>(c, sm, ALS_DUAL_SMALL);
+    return c->dual_warp ? launch_sweep_dual_warp(c, sm, ALS_DUAL_SMALL) : launch_dual<7>(c, sm, ALS_DUAL_SMALL);
 }
