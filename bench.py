@@ -427,6 +427,9 @@ def run_serving(args):
            f"(ratings {[len(j[4]) for j in jobs]})", "results": []}
     for prec in ("mixed", "fp64"):
         model = ALS(64, n_m, mrows, mi, mv, n_f, lam, precision=prec)
+        if args.launch and prec == "mixed":
+            model.set_launch(**{k: (v if k == "gram_path" and not v.isdigit() else int(v))
+                                for k, v in (kv.split("=") for kv in args.launch.split(","))})
         model.set_factors(np.zeros((64, n_f)), synth.init_factors(0, n_m, n_f, 7).reshape(n_m, n_f))
         torch.cuda.synchronize()
         for rate in rates:
