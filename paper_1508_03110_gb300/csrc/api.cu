@@ -109,7 +109,8 @@ void *mblk(const als_ctx *c, void *v) { return vrow(c, v, c->n_u); }
 
 // One half of P(x): side 0 solves users from the M rows in F_M, side 1 items
 // from the U rows in F_U.
-als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void *Xout, void *Gbar) {
+als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void *Xout, void *Gbar,
+                      void *Gout = nullptr) {
     SweepArgs a;
     a.ptr = side ? c->mptr : c->uptr;
     a.idx = side ? c->midx : c->uidx;
@@ -121,6 +122,7 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
     a.Xin = Xin;
     a.Xout = Xout;
     a.Gbar = Gbar;
+    a.Gout = Gout;
     a.nf = c->nf;
     a.ld = c->ld;
     a.lambda = c->cfg.lambda;
@@ -164,11 +166,22 @@ als_status half_sweep(als_ctx *c, int side, const void *F, const void *Xin, void
 }
 
 // xbar = P(x) with gbar = x - xbar, or in place (x <- P(x)) when Xout == X.
-als_status sweep_into(als_ctx *c, void *X, void *Xout, void *Gbar) {
-    als_status s = half_sweep(c, 0, mblk(c, X), ublk(c, X), ublk(c, Xout), Gbar ? ublk(c, Gbar) : nullptr);
+// G (may be null): with the fused gradient, the users' rows of grad f(X)
+// are written into G by the U half (its first residuals)
+als_status sweep_into(als_ctx *c, void *X, void *Xout, void *Gbar, void *G = nullptr) {
+    als_status s = half_sweep(c, 0, mblk(c, X), ublk(c, X), ublk(c, Xout), Gbar ? ublk(c, Gbar) : nullptr,
+                              G ? ublk(c, G) : nullptr);
     if (s != ALS_OK) return s;
     return half_sweep(c, 1, ublk(c, Xout), mblk(c, X), mblk(c, Xout), Gbar ? mblk(c, Gbar) : nullptr);
 }
+
+// The mixed tensor-core sweep forms, for every user row, the FP32 residual
+// r0 = sum_e f_e (r_e - f_e . x_i) at the current row, whose -2 (r0 -
+// lambda n_i x_i) is that row of grad f(x): so P(x) can write the users'
+// gradient rows and the gradient pass then forms only their FP64 terms (the
+// items' rows need U of x, not the new U of the sweep's first half).  The
+// FMA sweeps (FP64 form, n_f <= 32) form the right-hand side instead.
+bool fused_grad(const als_ctx *c) { return c->use_tc && !c->f64; }
 
 PassArgs pass_args(const als_ctx *c, int side) {
     PassArgs a;
@@ -189,7 +202,10 @@ PassArgs pass_args(const als_ctx *c, int side) {
 // gradient of Eq. (1) at X into Gout; per-row terms |g|^2, gbar.g,
 // gbar.(g-gprev) and, with P (the Hestenes-Stiefel form of beta-bar),
 // p.(g-gprev).  Gbar == Gout: gbar is the gradient itself (plain NCG).
-als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev, void *P = nullptr) {
+// users_written: the users' gradient rows are already in Gout (the fused
+// sweep), only their row terms are formed
+als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev, void *P = nullptr,
+                     bool users_written = false) {
     for (int side = 0; side < 2; ++side) {
         PassArgs a = pass_args(c, side);
         a.Xs = side ? mblk(c, X) : ublk(c, X);
@@ -200,6 +216,13 @@ als_status grad_into(als_ctx *c, void *X, void *Gout, void *Gbar, void *Gprev, v
         a.Ps = (P && Gprev) ? (side ? mblk(c, P) : ublk(c, P)) : nullptr;
         const int64_t n = side ? c->n_m : c->n_u;
         const int64_t nh = side ? c->nheavy_m : c->nheavy_u;
+        if (side == 0 && users_written) {
+            a.row_begin = 0;
+            a.nrows = n;
+            als_status s = launch_grad_terms(c, a);
+            if (s != ALS_OK) return s;
+            continue;
+        }
         a.row_begin = 0;
         a.nrows = nh;
         als_status s = launch_grad(c, a, true);
@@ -273,9 +296,10 @@ als_status ncg_init(als_ctx *c) {
         if (s != ALS_OK) return s;
         s = plain_gbar(c, c->G[c->gcur]);
     } else {
-        s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+        const bool fg = fused_grad(c);
+        s = sweep_into(c, c->X, c->Xbar, c->Gbar, fg ? c->G[c->gcur] : nullptr);
         if (s != ALS_OK) return s;
-        s = grad_into(c, c->X, c->G[c->gcur], c->Gbar, nullptr);
+        s = grad_into(c, c->X, c->G[c->gcur], c->Gbar, nullptr, nullptr, fg);
     }
     if (s != ALS_OK) return s;
     s = launch_reduce(c, 3, c->n_u + c->n_m, S_RED, POST_INIT, ls_params(c));
@@ -301,9 +325,10 @@ als_status ncg_iter(als_ctx *c, int gcur) {
         if (s != ALS_OK) return s;
         s = plain_gbar(c, c->G[gcur ^ 1]);
     } else {
-        s = sweep_into(c, c->X, c->Xbar, c->Gbar);
+        const bool fg = fused_grad(c);
+        s = sweep_into(c, c->X, c->Xbar, c->Gbar, fg ? c->G[gcur ^ 1] : nullptr);
         if (s != ALS_OK) return s;
-        s = grad_into(c, c->X, c->G[gcur ^ 1], c->Gbar, c->G[gcur], hs ? c->P : nullptr);
+        s = grad_into(c, c->X, c->G[gcur ^ 1], c->Gbar, c->G[gcur], hs ? c->P : nullptr, fg);
     }
     if (s != ALS_OK) return s;
     s = launch_reduce(c, hs ? 4 : 3, c->n_u + c->n_m, S_RED, POST_BETA, ls_params(c));

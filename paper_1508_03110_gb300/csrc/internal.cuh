@@ -228,6 +228,9 @@ struct SweepArgs {
     int64_t ndual = 0;
     int dual_nmax = 0;
     int64_t ndual_small = 0;   // ... the last of which have at most ALS_DUAL_SMALL ratings
+    // mixed form: the gradient rows g_i = -2 (r0 - lambda n_i x_i) of this half,
+    // r0 the first FP32 residual at the current row (nullptr: not written)
+    void *Gout = nullptr;
     // segment mode (split heavy rows): "row" r is segment r, a slice
     // [seg_beg[r], seg_beg[r] + seg_len[r]) of the ratings of row
     // order[seg_row[r]]; the kernel writes that slice's partial Gram matrix
@@ -270,6 +273,8 @@ struct PassArgs {
     int64_t stride, rowoff;
 };
 als_status launch_grad(als_ctx *c, const PassArgs &a, bool heavy);
+// the row terms of gradient rows already in a.Gout (rows 0 .. nrows - 1)
+als_status launch_grad_terms(als_ctx *c, const PassArgs &a);
 als_status launch_lscoef(als_ctx *c, const PassArgs &a, bool heavy);
 als_status launch_lscoef_reg(als_ctx *c, const PassArgs &a);  // rows without rating terms
 als_status launch_reduce(als_ctx *c, int nterms, int64_t n, int s_off, int post,

@@ -83,18 +83,15 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // ---------------------------------------------------------------------------
 // gradient
 // ---------------------------------------------------------------------------
+// the per-row FP64 terms of Eq. (8) from the row's gradient g (this lane's
+// 4-wide slot): |g|^2, gbar . g, gbar . (g - gprev) and, with Ps,
+// p . (g - gprev), summed over the group and written to rowterm
 template <typename T, int LPR>
-__device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
-                                            unsigned mask, const T (&x)[4], const T (&acc)[4]) {
+__device__ __forceinline__ void grad_terms(const PassArgs &a, int64_t row, int gl, unsigned mask, const T (&g)[4]) {
     const int nslot = a.ld / 4;
     const bool act = gl < nslot;
-    const T l2 = (T)(2.0 * a.lambda * (double)n);
-    T g[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) g[i] = l2 * x[i] - T(2) * acc[i];
     double tg = 0, tgb = 0, tgd = 0, tpd = 0;
     if (act) {
-        st4(reinterpret_cast<T *>(a.Gout) + row * a.ld + 4 * gl, g);
 #pragma unroll
         for (int i = 0; i < 4; ++i) tg += (double)g[i] * (double)g[i];
         if (a.Gbar) {
@@ -133,6 +130,34 @@ __device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int6
         a.rowterm[a.stride + o] = tgb;
         a.rowterm[2 * a.stride + o] = tgd;
         if (a.Ps) a.rowterm[3 * a.stride + o] = tpd;
+    }
+}
+
+// g_i = 2 lambda n_i x_i - 2 acc, stored, then its row terms
+template <typename T, int LPR>
+__device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
+                                            unsigned mask, const T (&x)[4], const T (&acc)[4]) {
+    const T l2 = (T)(2.0 * a.lambda * (double)n);
+    T g[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = l2 * x[i] - T(2) * acc[i];
+    if (gl < a.ld / 4) st4(reinterpret_cast<T *>(a.Gout) + row * a.ld + 4 * gl, g);
+    grad_terms<T, LPR>(a, row, gl, mask, g);
+}
+
+// the row terms of gradient rows already in Gout (the mixed tensor-core
+// sweep writes a side's gradient rows while it solves them: its first
+// residual is that gradient); rows 0 .. nrows - 1 of the side
+template <typename T, int LPR>
+__global__ void __launch_bounds__(256) k_grad_terms(PassArgs a) {
+    const int lane = threadIdx.x & 31, gl = lane % LPR;
+    const unsigned mask = group_mask<LPR>(lane);
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / LPR;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR; row < a.nrows; row += ngroups) {
+        T g[4];
+        if (gl < a.ld / 4) ld4(reinterpret_cast<const T *>(a.Gout) + row * a.ld + 4 * gl, g);
+        else zero4(g);
+        grad_terms<T, LPR>(a, row, gl, mask, g);
     }
 }
 
@@ -957,6 +982,27 @@ als_status grad_dispatch(als_ctx *c, const PassArgs &a, bool heavy) {
     }
 }
 
+template <typename T, int LPR>
+als_status grad_terms_launch(als_ctx *c, const PassArgs &a) {
+    if (a.nrows <= 0) return ALS_OK;
+    const int64_t groups_per_block = 256 / LPR;
+    const int64_t want = (a.nrows + groups_per_block - 1) / groups_per_block;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * c->grid_mult));
+    k_grad_terms<T, LPR><<<g, 256, 0, c->stream>>>(a);
+    ALS_CUDA_TRY(cudaGetLastError());
+    return ALS_OK;
+}
+
+template <typename T>
+als_status grad_terms_dispatch(als_ctx *c, const PassArgs &a) {
+    switch (lpr_for(a.ld)) {
+        case 4: return grad_terms_launch<T, 4>(c, a);
+        case 8: return grad_terms_launch<T, 8>(c, a);
+        case 16: return grad_terms_launch<T, 16>(c, a);
+        default: return grad_terms_launch<T, 32>(c, a);
+    }
+}
+
 template <typename T, bool HAS_P>
 als_status lscoef_dispatch(als_ctx *c, const PassArgs &a, int kind) {
     switch (lpr_for(a.ld)) {
@@ -971,6 +1017,10 @@ als_status lscoef_dispatch(als_ctx *c, const PassArgs &a, int kind) {
 
 als_status launch_grad(als_ctx *c, const PassArgs &a, bool heavy) {
     return c->f64 ? grad_dispatch<double>(c, a, heavy) : grad_dispatch<float>(c, a, heavy);
+}
+
+als_status launch_grad_terms(als_ctx *c, const PassArgs &a) {
+    return c->f64 ? grad_terms_dispatch<double>(c, a) : grad_terms_dispatch<float>(c, a);
 }
 
 als_status launch_lscoef(als_ctx *c, const PassArgs &a, bool heavy) {

@@ -151,6 +151,10 @@ __global__ void __launch_bounds__(DU_THREADS, MINB) k_sweep_dual(SweepArgs a, in
             // v = r0 - lambda n u0 (fixed order over the warps), zero past n_f
             for (int k = t; k < nf4; k += DU_THREADS)
                 v[k] = k < nf ? ((part[k] + part[128 + k]) + (part[256 + k] + part[384 + k])) - lam_n * u[k] : 0.0f;
+            // the row's gradient -2 (r0 - lambda n u0) (ld = nf4 slots)
+            if (a.Gout)
+                for (int k = t; k < a.ld; k += DU_THREADS)
+                    reinterpret_cast<float *>(a.Gout)[row * a.ld + k] = k < nf ? -2.0f * v[k] : 0.0f;
             // ---- 2. G = F F^T + lambda n I, lower triangle, 4 x 4 tiles ------
             {
                 const int nt = (n + 3) >> 2;
@@ -273,6 +277,7 @@ __global__ void __launch_bounds__(DU_THREADS, MINB) k_sweep_dual(SweepArgs a, in
             const float xk = xi ? xi[k] : 0.0f;
             xo[k] = uk;
             if (gb) gb[k] = xk - uk;
+            if (a.Gout && n <= 0) reinterpret_cast<float *>(a.Gout)[row * a.ld + k] = 0.0f;
         }
         __syncthreads();
     }

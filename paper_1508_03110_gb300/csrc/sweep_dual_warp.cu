@@ -71,7 +71,8 @@ __device__ __forceinline__ float warp_sum(float x) {
 // the unrolled factorisation and solves (rows past n: the identity).
 template <int R, int NB>
 __device__ __forceinline__ void dual_warp_row(const SweepArgs &a, float *Fs, float *Gs, float *us, float *vs, int S,
-                                              int64_t beg, int n, float lam_n, int lane, float (&u)[4], bool &ok) {
+                                              int64_t beg, int n, float lam_n, int lane, float (&u)[4], bool &ok,
+                                              float *go) {
     static_assert(NB <= 32 * R, "rows per lane");
     const int nf = a.nf, nf4 = (nf + 3) & ~3;
     const bool act = 4 * lane < nf4;
@@ -124,6 +125,9 @@ __device__ __forceinline__ void dual_warp_row(const SweepArgs &a, float *Fs, flo
     float v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = 4 * lane + i < nf ? (acc[i] - cmp[i]) - lam_n * u[i] : 0.0f;
+    // the row's gradient -2 (r0 - lambda n u0)
+    if (go && 4 * lane < a.ld)
+        *reinterpret_cast<float4 *>(go + 4 * lane) = make_float4(-2.0f * v[0], -2.0f * v[1], -2.0f * v[2], -2.0f * v[3]);
     __syncwarp();
     // ---- 2. G = F F^T (packed lower triangle), 2 x 2 tiles of rows ---------
     {
@@ -353,6 +357,7 @@ __global__ void __launch_bounds__(32 * wd_warps(R)) k_sweep_dual_warp(SweepArgs 
     const float *xi = a.Xin ? reinterpret_cast<const float *>(a.Xin) + row * a.ld : nullptr;
     float *xo = reinterpret_cast<float *>(a.Xout) + row * a.ld;
     float *gb = a.Gbar ? reinterpret_cast<float *>(a.Gbar) + row * a.ld : nullptr;
+    float *go = a.Gout ? reinterpret_cast<float *>(a.Gout) + row * a.ld : nullptr;
     const float lam_n = (float)(a.lambda * (double)n);
     // rows longer than the launch's bound are not this kernel's (the host
     // never passes one): they keep their value and count as not solved
@@ -363,10 +368,10 @@ __global__ void __launch_bounds__(32 * wd_warps(R)) k_sweep_dual_warp(SweepArgs 
     for (int i = 0; i < 4; ++i) u[i] = (xi && 4 * lane + i < nf) ? xi[4 * lane + i] : 0.0f;
     if (ok) {
         if constexpr (R == 1) {
-            if (n <= 16) dual_warp_row<1, 16>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok);
-            else dual_warp_row<1, 32>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok);
+            if (n <= 16) dual_warp_row<1, 16>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok, go);
+            else dual_warp_row<1, 32>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok, go);
         } else {
-            dual_warp_row<2, 64>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok);
+            dual_warp_row<2, 64>(a, Fs, Gs, us, vs, L.S, beg, n, lam_n, lane, u, ok, go);
         }
     }
     if (!ok) {
@@ -385,6 +390,7 @@ __global__ void __launch_bounds__(32 * wd_warps(R)) k_sweep_dual_warp(SweepArgs 
         *reinterpret_cast<float4 *>(xo + 4 * lane) = make_float4(o[0], o[1], o[2], o[3]);
         if (gb) *reinterpret_cast<float4 *>(gb + 4 * lane) = make_float4(xk[0] - o[0], xk[1] - o[1], xk[2] - o[2],
                                                                          xk[3] - o[3]);
+        if (go && n <= 0) *reinterpret_cast<float4 *>(go + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 

@@ -56,6 +56,7 @@ struct SplitArgs {
     double lambda;
     int more;                 // mixed: corrections still allowed after this one
     int seg_cap;              // the most ratings of any segment (seg_len)
+    void *Gout;               // mixed: the rows' gradient -2 (r0 - lambda n x_i), or null
 };
 
 constexpr int HT = 128;  // threads per CTA
@@ -106,6 +107,8 @@ __global__ void __launch_bounds__(HT) k_split_solve(SplitArgs s) {
         A[sizeof(T) == 8 ? t * ldA + t : tri_off(t) + t] += lam_n;
         if (sizeof(T) == 4) v1[t] -= lam_n * u[t];  // mixed: residual at x_i
     }
+    if (sizeof(T) == 4 && s.Gout && t < s.ld)
+        reinterpret_cast<float *>(s.Gout)[row * s.ld + t] = t < nf ? -2.0f * (float)v1[t] : 0.0f;
     __syncthreads();
     bool ok;
     if constexpr (sizeof(T) == 8) {
@@ -364,6 +367,7 @@ als_status split_sweep_launches(als_ctx *c, const SweepArgs &a, int side, cudaSt
     b.seg_out = c->seg_part;
     b.seg_stride = c->seg_stride;
     b.nrows = S;
+    b.Gout = nullptr;  // a segment's residual is a partial
     als_status st = launch_sweep(c, b, c->f64, c->use_tc);
     if (st != ALS_OK) return st;
     // 2. per split row: sum, factor, solve
@@ -390,6 +394,7 @@ als_status split_sweep_launches(als_ctx *c, const SweepArgs &a, int side, cudaSt
     s.lambda = a.lambda;
     s.more = a.refine - 1;
     s.seg_cap = c->seg_len;
+    s.Gout = a.Gout;
     const size_t smem = solve_smem(a.nf, c->esz);
     if (c->f64) {
         if (raise_smem_limit((const void *)k_split_solve<double>, smem) != ALS_OK) return ALS_ECUDA;

@@ -27,6 +27,9 @@
 // With the launch shape chol_tc, steps 3-4 factor A in place in TMEM instead
 // (chol_tmem: panels of 16 columns, trailing updates as tcgen05 MMAs), and the
 // CTA holds its TMEM columns until the factorisation ends.
+// With a.Gout the kernel also writes the row's gradient of Eq. (1) at the
+// current factors, -2 v1 with v1 = r0 - lambda n_i x_i the first residual:
+// the gradient pass then only forms the rows' FP64 terms.
 // Every mbarrier wait is bounded (%globaltimer): on expiry the CTA gives each
 // stage whose MMAs may still be in flight one more bounded wait, records a
 // timeout, frees its TMEM and returns.  The rows of such a launch are not
@@ -333,6 +336,9 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
         const float *xi = a.Xin ? reinterpret_cast<const float *>(a.Xin) + row * a.ld : nullptr;
         float *xo = reinterpret_cast<float *>(a.Xout) + row * a.ld;
         float *gb = a.Gbar ? reinterpret_cast<float *>(a.Gbar) + row * a.ld : nullptr;
+        // the row's gradient g_i = 2 lambda n_i x_i - 2 r0 = -2 v1, v1 the first
+        // residual below (whole rows only: a segment's is a partial)
+        float *go = (a.Gout && !seg) ? reinterpret_cast<float *>(a.Gout) + row * a.ld : nullptr;
         const float lam_n = (float)(a.lambda * (double)n);
         bool ok = n > 0;
         // current row u0 = x_i (fold-in: 0), one 4-wide slot per lane
@@ -610,6 +616,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                 // the warps)
                 __syncthreads();
                 if (t < nf) v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
+                if (go && t < a.ld) go[t] = t < nf ? -2.0f * v1[t] : 0.0f;
                 // ---- 3-4. Cholesky of A = D + lambda n I from TMEM, trailing
                 //      updates on the tensor core --------------------------------
                 ok = chol_tmem(tmem, nf, ntc, lam_n, A, diag, work + 512, sbase + (uint32_t)L.ops, mbar[0],
@@ -632,6 +639,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
                     A[tri_off(t) + t] += lam_n;
                     v1[t] = ((part[t] + part[128 + t]) + (part[256 + t] + part[384 + t])) - lam_n * u[t];
                 }
+                if (go && t < a.ld) go[t] = t < nf ? -2.0f * v1[t] : 0.0f;
                 __syncthreads();
                 // ---- 4. blocked Cholesky of A in shared memory ---------------
                 ok = chol_blocked128(A, nf, diag, work, t, 32 * (int)(blockIdx.x & 3));
@@ -665,6 +673,7 @@ __global__ void __launch_bounds__(TC_THREADS, tc_min_blocks(PFM, KC))
             const float xk = xi ? xi[k] : 0.0f;
             xo[k] = uk;
             if (gb) gb[k] = xk - uk;
+            if (go && n <= 0) go[k] = 0.0f;  // no ratings: the gradient row is 0
         }
         __syncthreads();
     }
