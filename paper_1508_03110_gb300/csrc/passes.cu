@@ -80,6 +80,46 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     }
 }
 
+// Totals over the group of each of N FP64 values, in every lane of the group.
+// A whole warp halves the values at each of its first log2(P) exchanges (P =
+// N rounded up to 4 or 8), so that each lane then carries one value summed
+// over 2, 4 or 8 lanes; the remaining exchanges finish it and P reads gather
+// the totals (6 or 9 additions in all instead of 5 N, on the slow FP64 pipe).
+// Smaller groups add each value over their own exchanges.
+template <int LPR, int N>
+__device__ __forceinline__ void tsum_n(double (&t)[N], unsigned mask, int lane) {
+    if constexpr (LPR == 32 && N >= 3 && N <= 8) {
+        constexpr int P = N <= 4 ? 4 : 8;
+        double d[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) d[i] = i < N ? t[i] : 0.0;
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+        double e[P / 2];
+#pragma unroll
+        for (int i = 0; i < P / 2; ++i)
+            e[i] = (b4 ? d[i + P / 2] : d[i]) + __shfl_xor_sync(mask, b4 ? d[i] : d[i + P / 2], 16);
+        double f[P / 4];
+#pragma unroll
+        for (int i = 0; i < P / 4; ++i)
+            f[i] = (b3 ? e[i + P / 4] : e[i]) + __shfl_xor_sync(mask, b3 ? e[i] : e[i + P / 4], 8);
+        double v;
+        if constexpr (P == 8) v = (b2 ? f[1] : f[0]) + __shfl_xor_sync(mask, b2 ? f[0] : f[1], 4);
+        else v = f[0] + __shfl_xor_sync(mask, f[0], 4);
+        v += __shfl_xor_sync(mask, v, 2);
+        v += __shfl_xor_sync(mask, v, 1);
+        // lane l now holds the total of value 4 b4 + 2 b3 + b2 (P = 8) or
+        // 2 b4 + b3 (P = 4)
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            t[q] = __shfl_sync(mask, v,
+                               P == 8 ? ((q >> 2) & 1) * 16 + ((q >> 1) & 1) * 8 + (q & 1) * 4
+                                      : ((q >> 1) & 1) * 16 + (q & 1) * 8);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) t[q] = gsum<LPR>(t[q], mask);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // gradient
 // ---------------------------------------------------------------------------
@@ -87,7 +127,8 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // 4-wide slot): |g|^2, gbar . g, gbar . (g - gprev) and, with Ps,
 // p . (g - gprev), summed over the group and written to rowterm
 template <typename T, int LPR>
-__device__ __forceinline__ void grad_terms(const PassArgs &a, int64_t row, int gl, unsigned mask, const T (&g)[4]) {
+__device__ __forceinline__ void grad_terms(const PassArgs &a, int64_t row, int gl, int lane, unsigned mask,
+                                           const T (&g)[4]) {
     const int nslot = a.ld / 4;
     const bool act = gl < nslot;
     double tg = 0, tgb = 0, tgd = 0, tpd = 0;
@@ -120,29 +161,27 @@ __device__ __forceinline__ void grad_terms(const PassArgs &a, int64_t row, int g
             }
         }
     }
-    tg = gsum<LPR>(tg, mask);
-    tgb = gsum<LPR>(tgb, mask);
-    tgd = gsum<LPR>(tgd, mask);
-    if (a.Ps) tpd = gsum<LPR>(tpd, mask);
+    double tt[4] = {tg, tgb, tgd, tpd};
+    tsum_n<LPR, 4>(tt, mask, lane);
     if (gl == 0) {
         const int64_t o = a.rowoff + row;
-        a.rowterm[o] = tg;
-        a.rowterm[a.stride + o] = tgb;
-        a.rowterm[2 * a.stride + o] = tgd;
-        if (a.Ps) a.rowterm[3 * a.stride + o] = tpd;
+        a.rowterm[o] = tt[0];
+        a.rowterm[a.stride + o] = tt[1];
+        a.rowterm[2 * a.stride + o] = tt[2];
+        if (a.Ps) a.rowterm[3 * a.stride + o] = tt[3];
     }
 }
 
 // g_i = 2 lambda n_i x_i - 2 acc, stored, then its row terms
 template <typename T, int LPR>
-__device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
+__device__ __forceinline__ void grad_finish(const PassArgs &a, int64_t row, int64_t n, int gl, int lane,
                                             unsigned mask, const T (&x)[4], const T (&acc)[4]) {
     const T l2 = (T)(2.0 * a.lambda * (double)n);
     T g[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) g[i] = l2 * x[i] - T(2) * acc[i];
     if (gl < a.ld / 4) st4(reinterpret_cast<T *>(a.Gout) + row * a.ld + 4 * gl, g);
-    grad_terms<T, LPR>(a, row, gl, mask, g);
+    grad_terms<T, LPR>(a, row, gl, lane, mask, g);
 }
 
 // the row terms of gradient rows already in Gout (the mixed tensor-core
@@ -157,7 +196,7 @@ __global__ void __launch_bounds__(256) k_grad_terms(PassArgs a) {
         T g[4];
         if (gl < a.ld / 4) ld4(reinterpret_cast<const T *>(a.Gout) + row * a.ld + 4 * gl, g);
         else zero4(g);
-        grad_terms<T, LPR>(a, row, gl, mask, g);
+        grad_terms<T, LPR>(a, row, gl, lane, mask, g);
     }
 }
 
@@ -240,7 +279,7 @@ __global__ void __launch_bounds__(256) k_grad(PassArgs a) {
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[i] -= cmp[i];
-        grad_finish<T, LPR>(a, row, n, gl, mask, x, acc);
+        grad_finish<T, LPR>(a, row, n, gl, lane, mask, x, acc);
     }
 }
 
@@ -283,7 +322,7 @@ __global__ void __launch_bounds__(256) k_grad_heavy(PassArgs a) {
             for (int q = 0; q < NG; ++q)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) tot[i] += part[q][gl][i];
-            grad_finish<T, LPR>(a, row, n, gl, mask, x, tot);
+            grad_finish<T, LPR>(a, row, n, gl, lane, mask, x, tot);
         }
         __syncthreads();
     }
@@ -392,14 +431,11 @@ __device__ __forceinline__ void lscoef_range(const PassArgs &a, const T (&xu)[4]
         lscoef_rating<T, LPR, HAS_P>(xu, pu, Xo, Po, a.idx[e], a.val[e], a.ld, gl, act, mask, owner, q, t);
 }
 
-template <int LPR>
-__device__ __forceinline__ void tsum5(double (&t)[5], unsigned mask) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) t[q] = gsum<LPR>(t[q], mask);
-}
-
+// t: this lane's shares of the five rating terms; the row's regulariser
+// lambda n_i |x + alpha p|^2 adds this lane's slots of x.x, 2 x.p and p.p
+// to them, and one reduction over the group gives the row's five terms
 template <typename T, int LPR, bool HAS_P>
-__device__ __forceinline__ void lscoef_finish(const PassArgs &a, int64_t row, int64_t n, int gl,
+__device__ __forceinline__ void lscoef_finish(const PassArgs &a, int64_t row, int64_t n, int gl, int lane,
                                               unsigned mask, const T (&xu)[4], const T (&pu)[4],
                                               double (&t)[5]) {
     double xx = 0, xp = 0, pp = 0;
@@ -411,16 +447,14 @@ __device__ __forceinline__ void lscoef_finish(const PassArgs &a, int64_t row, in
             pp += (double)pu[i] * (double)pu[i];
         }
     }
-    xx = gsum<LPR>(xx, mask);
-    if (HAS_P) {
-        xp = gsum<LPR>(xp, mask);
-        pp = gsum<LPR>(pp, mask);
-    }
     const double ln = a.lambda * (double)n;
     t[0] += ln * xx;
     if (HAS_P) {
         t[1] += ln * 2.0 * xp;
         t[2] += ln * pp;
+        tsum_n<LPR, 5>(t, mask, lane);
+    } else {
+        t[0] = gsum<LPR>(t[0], mask);
     }
     if (gl == 0) {
         const int64_t o = a.rowoff + row;
@@ -453,8 +487,7 @@ __global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
         q.have = false;
         lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, beg, beg + n, gl, lane, act, mask, owner, q, t);
         ls_flush<T, HAS_P>(q, t);
-        tsum5<LPR>(t, mask);
-        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
+        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, lane, mask, xu, pu, t);
     }
 }
 
@@ -485,15 +518,18 @@ __global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
         q.have = false;
         lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, e0, e1, gl, lane, act, mask, owner, q, t);
         ls_flush<T, HAS_P>(q, t);
-        tsum5<LPR>(t, mask);
+        if constexpr (HAS_P) tsum_n<LPR, 5>(t, mask, lane);
+        else t[0] = gsum<LPR>(t[0], mask);
         if (gl == 0)
             for (int q = 0; q < 5; ++q) part[gi][q] = t[q];
         __syncthreads();
         if (gi == 0) {
+            // the groups' sums in group order, as lane 0's share
             double tot[5] = {0, 0, 0, 0, 0};
-            for (int q = 0; q < NG; ++q)
-                for (int s = 0; s < 5; ++s) tot[s] += part[q][s];
-            lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, tot);
+            if (gl == 0)
+                for (int q = 0; q < NG; ++q)
+                    for (int s = 0; s < 5; ++s) tot[s] += part[q][s];
+            lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, lane, mask, xu, pu, tot);
         }
         __syncthreads();
     }
@@ -517,7 +553,7 @@ __global__ void __launch_bounds__(256) k_lscoef_reg(PassArgs a) {
             zero4(xu); zero4(pu);
         }
         double t[5] = {0, 0, 0, 0, 0};
-        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, mask, xu, pu, t);
+        lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, lane, mask, xu, pu, t);
         if (HAS_P && gl == 0) {
             a.rowterm[3 * a.stride + a.rowoff + row] = 0.0;
             a.rowterm[4 * a.stride + a.rowoff + row] = 0.0;
