@@ -130,29 +130,3 @@ def test_chol_tc_foldin_matches_the_oracle(tiny):
     assert _mixed_row_excess(u, ref, np.zeros_like(ref), kap, 1e-6) < 1.0
     assert _row_rel(u, ref, n_f) < 1e-6
 
-
-@pytest.mark.parametrize("split", [False, True])
-def test_fused_users_gradient_matches_the_gradient_pass(tiny, split):
-    """The mixed tensor-core sweep writes the users' gradient rows from its
-    first residual (-2 (r0 - lambda n_i x_i)); after an ALS-NCG step the
-    state's gradient equals what the gradient pass forms at the same x, row
-    by row to FP32 rounding, with split rows too."""
-    r = tiny
-    n_f = 100
-    x0 = synth.init_factors(r.n_u, r.n_m, n_f, 21)
-    with _als(r, n_f) as m:
-        if split:
-            m.set_launch(split_min=256, seg_len=64)
-        m.set_x(x0)
-        for _ in range(3):
-            m.step(info=False)
-        st = m.get_state()
-        g_pass, _ = m.grad()
-    gf = st["g"].reshape(-1, n_f)[: r.n_u]
-    gp = np.asarray(g_pass).reshape(-1, n_f)[: r.n_u]
-    P = oracle.build_problem(r.n_u, r.n_m, n_f, r.lam, r.rows, r.cols, r.vals)
-    g_ref = oracle.grad(P, st["x"]).reshape(-1, n_f)[: r.n_u]
-    err = np.linalg.norm(gf - gp, axis=1)
-    scale = np.maximum(np.linalg.norm(g_ref, axis=1), 1e-3 * np.median(np.linalg.norm(g_ref, axis=1)))
-    assert np.max(err / scale) < 1e-4, np.max(err / scale)
-    assert np.max(np.linalg.norm(gf - g_ref, axis=1) / scale) < 1e-4
