@@ -411,7 +411,7 @@ typedef struct {
     int32_t dual_max;         /* default 64     */
     int32_t gather_tma;       /* default 0      */
     int32_t tc_chunk;         /* default 32     */
-    int32_t chol_tc;          /* default 0      */
+    int32_t chol_tc;          /* default 1      */
     int32_t dual_warp;        /* default 1      */
 } als_launch;
 
@@ -431,10 +431,13 @@ typedef struct {
 
 /* Time candidate shapes on this context's own data, at its current factors
  * and direction, one parameter group at a time (pass threshold and grid cap;
- * Gram path where both apply; split threshold and segment length; light-row
- * bound of the tensor-core sweep; FMA degree bin), and keep the fastest.  No factor, direction or NCG state is modified.
- * reps (1..100): timed repetitions per candidate, best kept.  out may be
- * NULL. */
+ * Gram path where both apply; split threshold and segment length; the
+ * tensor-core sweep's gather, chunk and factorisation; light-row bound and
+ * kernel; FMA degree bin), and keep the fastest.  A candidate replaces the
+ * shape kept so far only when it is at least 2% faster, so that timing noise
+ * does not choose between near-equal shapes.  No factor, direction or NCG
+ * state is modified.  reps (1..100): timed repetitions per candidate, best
+ * kept.  out may be NULL. */
 ALS_API als_status als_autotune(als_ctx *ctx, int32_t reps, als_tune_report *out);
 
 /* Groups: run max_iter ALS-NCG iterations (Algorithm 2) of n distinct

@@ -1233,7 +1233,7 @@ extern "C" als_status als_autotune(als_ctx *c, int32_t reps, als_tune_report *ou
         st = pass ? time_best_ms(c, reps, passes, &ms) : time_best_ms(c, reps, sweep, &ms);
         if (st != ALS_OK) return st;
         ++rep.candidates;
-        if (ms < best) {
+        if (ms < best * (1.0 - ALS_TUNE_MARGIN)) {
             best = ms;
             cur = cand;
         }

@@ -17,6 +17,7 @@
 #define ALS_DUAL_MAX 64        // longest row of the mixed form's light-row (n_i x n_i) solve
 #define ALS_DUAL_SMALL 32      // light rows at most this long take a smaller layout (more CTAs per SM)
 #define ALS_TC_PF_MIN 256      // tensor-core sweep: rows at least this long prefetch their factor rows
+#define ALS_TUNE_MARGIN 0.02   // the autotuner keeps a shape unless a candidate is this much faster
 
 // Slots of the device scalar block (double S[]).
 enum {
@@ -117,7 +118,7 @@ struct als_ctx {
     int grid_mult = 32;                // pass grids: at most grid_mult x sm_count CTAs
     int sweep_bin_min = 0;             // FMA sweep, n_f <= 32: rows with >= this many ratings use a CTA (0: none)
     int64_t sweep_big[2] = {0, 0};     // ... their count per side (a prefix of the degree order)
-    int chol_tc = 0;
+    int chol_tc = 1;
     int dual_warp = 1;                 // light rows of <= ALS_DUAL_SMALL ratings: a warp per row (1)                   // tensor-core sweep: Cholesky from TMEM, trailing updates as MMAs (1)
     int tc_chunk16 = 0;                // tensor-core sweep, rows below 256 ratings: chunks of 16 ratings (1) or 32 (0)
     int gather_tma = 0;                // tensor-core sweep: heavy rows' factor rows gathered by TMA (1)
