@@ -619,19 +619,27 @@ def tune_warm(m, x0, reps, warm=10):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the sweep
-# kernels' launches from one ncu capture of this command's workload, summed
-# over one sweep's launches of that kernel, with the SHA-256 (first 16 hex
-# digits) of the kernel's sources and the launch shapes of the capture.  A
-# figure is reported only while those sources are unchanged and the bench
-# runs with the same shapes (the autotuner's choice; another choice gives
-# other launches).
-SHAPES_ML20M = "chol_tc=1,dual_max=64,dual_warp=1,gather_tma=1,gram_path=2,seg_len=1024,split_min=2048,tc_chunk=32"
-# Captured on a GB300 (profiles/sweep_dram_traffic_ml20m.md): the 6 launches
-# of k_sweep_tc in one sweep (two of them the split rows' segments, which
-# write their partials) read 708.8 MB and wrote 387.0 MB; the 4 light-row
-# launches (k_sweep_dual, k_sweep_dual_warp) read 131.8 MB and wrote 9.3 MB.
-TRAFFIC = {"k_sweep_tc": ("cf75ac8d274ef94b", SHAPES_ML20M, 1095828224),
-           "k_sweep_dual": ("4a34480ef6301d6e", SHAPES_ML20M, 141048064)}
+# kernels' launches from ncu captures of this command's workload, summed over
+# one sweep's launches of that kernel, with the SHA-256 (first 16 hex digits)
+# of the kernel's sources and the launch shapes of the capture.  A figure is
+# reported only while those sources are unchanged and the bench runs with the
+# same shapes (the autotuner's choice; another choice gives other launches).
+# The two sweep shapes below differ only in how k_sweep_tc gathers the factor
+# rows of rows >= 256 ratings: TMA (tile::gather4) or cp.async; the tuner
+# finds them within 0.5% of each other and may take either.
+SHAPES_ML20M_TMA = "chol_tc=1,dual_max=64,dual_warp=1,gather_tma=1,gram_path=2,seg_len=1024,split_min=2048,tc_chunk=32"
+SHAPES_ML20M_CPA = "chol_tc=1,dual_max=64,dual_warp=1,gather_tma=0,gram_path=2,seg_len=1024,split_min=2048,tc_chunk=32"
+# Captured on a GB300 (profiles/sweep_dram_traffic_ml20m.md), per sweep:
+# - TMA gather: the 6 launches of k_sweep_tc (two of them the split rows'
+#   segments, which write their partials) read 708.8 MB and wrote 387.0 MB;
+#   the 4 light-row launches (k_sweep_dual, k_sweep_dual_warp) read 131.8 MB
+#   and wrote 9.3 MB;
+# - cp.async gather: k_sweep_tc read 698.4 MB and wrote 386.3 MB; the light
+#   rows read 131.9 MB and wrote 9.4 MB.
+TRAFFIC = {"k_sweep_tc": (("cf75ac8d274ef94b", SHAPES_ML20M_TMA, 1095828224),
+                          ("cf75ac8d274ef94b", SHAPES_ML20M_CPA, 1084691712)),
+           "k_sweep_dual": (("4a34480ef6301d6e", SHAPES_ML20M_TMA, 141048064),
+                            ("4a34480ef6301d6e", SHAPES_ML20M_CPA, 141310464))}
 TRAFFIC_SOURCES = {"k_sweep_tc": ("sweep_tc.cu", "sweep_common.cuh", "tc_ptx.cuh"),
                    "k_sweep_dual": ("sweep_dual.cu", "sweep_common.cuh")}
 
@@ -657,10 +665,13 @@ def shapes_key(launch):
 def traffic_for(name, launches, launch):
     """DRAM bytes per launch of `name` (its captured per-sweep total over its
     launches), or None if not captured for the current sources and shapes."""
-    t = TRAFFIC.get(name)
-    if not t or t[0] != kernel_source_sha(name) or t[1] != shapes_key(launch) or launches < 1:
+    if launches < 1 or name not in TRAFFIC:
         return None
-    return t[2] / launches
+    sha, key = kernel_source_sha(name), shapes_key(launch)
+    for t in TRAFFIC.get(name, ()):
+        if t[0] == sha and t[1] == key:
+            return t[2] / launches
+    return None
 
 
 def load_peaks():

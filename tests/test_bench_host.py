@@ -50,3 +50,23 @@ def test_sweep_flops_per_row_formulation():
     t64f, g64f = b.sweep_flops(r, nf, 2, "fp64", 64)
     assert g64f == 0.0
     assert np.isclose(t64f, b.sweep_flops(r, nf, 2, "fp64", 0)[0])
+
+
+def test_traffic_only_for_captured_sources_and_shapes():
+    """`traffic` is the captured per-sweep DRAM bytes over the launches of one
+    sweep, and only for the sources and sweep shapes of a capture."""
+    b = _bench()
+    launch = dict(heavy_min=512, grid_mult=32, sweep_bin_min=0, split_min=2048, seg_len=1024,
+                  gram_path=2, dual_max=64, dual_warp=1, tc_chunk=32, chol_tc=1)
+    sha = b.kernel_source_sha("k_sweep_tc")
+    for gt in (0, 1):
+        launch["gather_tma"] = gt
+        key = b.shapes_key(launch)
+        want = [t[2] for t in b.TRAFFIC["k_sweep_tc"] if t[0] == sha and t[1] == key]
+        got = b.traffic_for("k_sweep_tc", 6, launch)
+        assert got == (want[0] / 6 if want else None)
+        # the passes' shapes do not decide the sweep's launches
+        assert b.traffic_for("k_sweep_tc", 6, dict(launch, heavy_min=1024, grid_mult=64)) == got
+    assert b.traffic_for("k_sweep_tc", 6, dict(launch, seg_len=512)) is None
+    assert b.traffic_for("k_sweep_tc", 0, launch) is None
+    assert b.traffic_for("k_sweep_none", 6, launch) is None
