@@ -1018,17 +1018,24 @@ def main():
         rows, cols, vals = np.ascontiguousarray(r.rows), np.ascontiguousarray(r.cols), np.ascontiguousarray(r.vals)
         t0 = time.perf_counter()
         me = ALS(r.n_u, r.n_m, rows, cols, vals, r.n_f, r.lam, **kw)
+        me.sync()
+        t1 = time.perf_counter()
         me.set_x(x0)
+        me.sync()
+        t2 = time.perf_counter()
         me.run(args.steps, 0.0, check_every=args.steps)
+        t3 = time.perf_counter()
         U, M = me.get_factors()
         te = time.perf_counter() - t0
         me.close()
+        parts = {"create": t1 - t0, "set_x": t2 - t1, "iterations": t3 - t2, "get_factors": t0 + te - t3}
         te = max_over_ranks(te, dist)
         h2d = r.nnz * 12 + x0.nbytes
         d2h = U.nbytes + M.nbytes
         e2e = {"value": job_throughput(r.nnz * args.steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
-               "includes": "context build from host COO, x0 upload, K iterations, factor download"}
+               "includes": "context build from host COO, x0 upload, K iterations, factor download",
+               "parts_ms": {k: round(v * 1e3, 2) for k, v in parts.items()}}
 
     # ---- seconds to tolerance from the same x_0 (the metric's headline) ----
     s2t = None
