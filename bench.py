@@ -13,7 +13,8 @@ value  = ratings x iterations / second over the timed steps, summed over ranks
          (inputs resident in HBM before the timed region starts);
 e2e    = the same metric through the C ABI with host buffers: building the
          context from host COO arrays, setting x_0 from the host, the
-         iterations, and reading the factors back, all inside the timed region;
+         iterations, and reading the factors back, all inside the timed region
+         (the median of three such jobs);
 roofline = the fused sweep kernel (the dominant launch) against the measured
          peak of the unit that bounds it;
 cpu_baseline = the FP64 oracle on the host cores, on a bounded sample.
@@ -618,6 +619,11 @@ def tune_warm(m, x0, reps, warm=10):
     return tune
 
 
+# whole end-to-end jobs timed; the bench reports the median (one job is
+# about half a second, and a single one moved by 20% between runs)
+E2E_RUNS = 3
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the sweep
 # kernels' launches from ncu captures of this command's workload, summed over
 # one sweep's launches of that kernel, with the SHA-256 (first 16 hex digits)
@@ -1016,25 +1022,31 @@ def main():
     if not args.no_e2e:
         barrier()
         rows, cols, vals = np.ascontiguousarray(r.rows), np.ascontiguousarray(r.cols), np.ascontiguousarray(r.vals)
-        t0 = time.perf_counter()
-        me = ALS(r.n_u, r.n_m, rows, cols, vals, r.n_f, r.lam, **kw)
-        me.sync()
-        t1 = time.perf_counter()
-        me.set_x(x0)
-        me.sync()
-        t2 = time.perf_counter()
-        me.run(args.steps, 0.0, check_every=args.steps)
-        t3 = time.perf_counter()
-        U, M = me.get_factors()
-        te = time.perf_counter() - t0
-        me.close()
-        parts = {"create": t1 - t0, "set_x": t2 - t1, "iterations": t3 - t2, "get_factors": t0 + te - t3}
-        te = max_over_ranks(te, dist)
+        runs = []
+        for _ in range(E2E_RUNS):
+            t0 = time.perf_counter()
+            me = ALS(r.n_u, r.n_m, rows, cols, vals, r.n_f, r.lam, **kw)
+            me.sync()
+            t1 = time.perf_counter()
+            me.set_x(x0)
+            me.sync()
+            t2 = time.perf_counter()
+            me.run(args.steps, 0.0, check_every=args.steps)
+            t3 = time.perf_counter()
+            U, M = me.get_factors()
+            te = time.perf_counter() - t0
+            me.close()
+            te = max_over_ranks(te, dist)
+            runs.append((te, {"create": t1 - t0, "set_x": t2 - t1, "iterations": t3 - t2,
+                              "get_factors": t0 + te - t3}))
+        te, parts = sorted(runs, key=lambda q: q[0])[len(runs) // 2]
         h2d = r.nnz * 12 + x0.nbytes
         d2h = U.nbytes + M.nbytes
         e2e = {"value": job_throughput(r.nnz * args.steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context build from host COO, x0 upload, K iterations, factor download",
+               "runs": f"the median of {E2E_RUNS} whole jobs",
+               "job_ms": [round(q[0] * 1e3, 2) for q in runs],
                "parts_ms": {k: round(v * 1e3, 2) for k, v in parts.items()}}
 
     # ---- seconds to tolerance from the same x_0 (the metric's headline) ----
