@@ -201,7 +201,9 @@ ALS_API als_status als_get_ratings(als_ctx *ctx, int64_t *uptr, int32_t *uidx, f
                            int32_t *midx, float *mval, int32_t *uorder, int32_t *morder);
 
 /* Set x (Eq. 5) from U (n_u x n_f) and M (n_m x n_f) of the given dtype.
- * Resets the ALS-NCG state (the next alsncg_step starts Algorithm 2 anew). */
+ * Resets the ALS-NCG state (the next alsncg_step starts Algorithm 2 anew).
+ * Synchronous for host sources (pageable or pinned): they may be reused when
+ * the call returns. */
 ALS_API als_status als_set_factors(als_ctx *ctx, const void *U, const void *M, int dtype,
                            int on_device);
 

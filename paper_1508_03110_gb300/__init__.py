@@ -198,8 +198,34 @@ class ALS:
         x = np.asarray(x, np.float64).reshape(self.n_u + self.n_m, self.n_f)
         self.set_factors(x[:self.n_u], x[self.n_u:])
 
-    def get_factors(self, dtype="float64", device=False):
+    def get_factors(self, dtype="float64", device=False, out=None):
+        """U (n_u x n_f) and M (n_m x n_f) as `dtype`, on the device (torch)
+        or the host (numpy).  `out` = (U, M): contiguous arrays of that dtype
+        and shape to write into instead, numpy arrays or torch tensors (CPU,
+        for example pinned, or CUDA); returned as given."""
         torch = _torch()
+        if out is not None:
+            U, M = out
+            want = (self.n_u, self.n_f), (self.n_m, self.n_f)
+            dt = ALS_DT_F64 if dtype == "float64" else ALS_DT_F32
+            ptrs, devs = [], []
+            for a, shape in zip((U, M), want):
+                if isinstance(a, torch.Tensor):
+                    ok = (a.is_contiguous() and tuple(a.shape) == shape
+                          and a.dtype == (torch.float64 if dt == ALS_DT_F64 else torch.float32))
+                    ptrs.append(a.data_ptr()); devs.append(1 if a.is_cuda else 0)
+                else:
+                    ok = (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.shape == shape
+                          and a.dtype == (np.float64 if dt == ALS_DT_F64 else np.float32))
+                    ptrs.append(a.ctypes.data if ok else 0); devs.append(0)
+                if not ok:
+                    raise ValueError(f"get_factors: out arrays must be contiguous {dtype} of shapes {want}")
+            if devs[0] != devs[1]:
+                raise ValueError("get_factors: out arrays must both be on the host or both on the device")
+            _lib.check(self.lib.als_get_factors(self.ctx, ptrs[0], ptrs[1], dt, devs[0]), "als_get_factors")
+            if devs[0]:
+                self.sync()
+            return U, M
         if device:
             tdt = torch.float64 if dtype == "float64" else torch.float32
             U = torch.empty((self.n_u, self.n_f), dtype=tdt, device="cuda")

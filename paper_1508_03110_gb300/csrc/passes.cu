@@ -342,20 +342,81 @@ struct LsPending {
     bool have;
 };
 
-template <typename T, bool HAS_P>
-__device__ __forceinline__ void ls_flush(LsPending<T> &q, double (&t)[5]) {
-    if (!q.have) return;
-    const double e0 = (double)q.r - (double)q.d0;
-    if (HAS_P) {
-        const double aa = (double)q.d1 + (double)q.d2, b = (double)q.d3;
-        t[0] += e0 * e0;
-        t[1] += -2.0 * e0 * aa;
-        t[2] += aa * aa - 2.0 * e0 * b;
-        t[3] += 2.0 * aa * b;
-        t[4] += b * b;
-    } else {
-        t[0] += e0 * e0;
+// A lane's sums of the five rating terms of Q.  FP64 form: FP64 terms, FP64
+// sums.  Mixed form: the terms are formed in FP32 from the FP32 dot products
+// (one rounding each, below the dot products' own error), every product is
+// split exactly into two floats (x y = p + e, e = fma(x, y, -p)) and the sums
+// are kept as float pairs (hi, lo) by Knuth's two-sum, which carries the
+// rounding error of every addition (Knuth, TAOCP vol. 2, 4.2.2; Dekker 1971).
+// That keeps a lane's sum near FP64 accuracy while the FP64 pipe, 1/64 of
+// the FP32 rate here, is used once per row (to add hi and lo) instead of
+// about 17 times per 32 ratings.
+template <typename T>
+struct LsAcc {
+    double t[5];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t[q] = 0.0;
     }
+    template <bool HAS_P>
+    __device__ __forceinline__ void add(const LsPending<T> &p) {
+        const double e0 = (double)p.r - (double)p.d0;
+        if (HAS_P) {
+            const double aa = (double)p.d1 + (double)p.d2, b = (double)p.d3;
+            t[0] += e0 * e0;
+            t[1] += -2.0 * e0 * aa;
+            t[2] += aa * aa - 2.0 * e0 * b;
+            t[3] += 2.0 * aa * b;
+            t[4] += b * b;
+        } else {
+            t[0] += e0 * e0;
+        }
+    }
+    __device__ __forceinline__ void out(double (&o)[5]) const {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) o[q] = t[q];
+    }
+};
+
+template <>
+struct LsAcc<float> {
+    float h[5], l[5];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) h[q] = l[q] = 0.0f;
+    }
+    // (h, l) += x y; the _rn intrinsics are never contracted into an FMA,
+    // which would break the exact splits
+    __device__ __forceinline__ void prod(int q, float x, float y) {
+        const float p = __fmul_rn(x, y), e = fmaf(x, y, -p);
+        const float s = __fadd_rn(h[q], p), bv = __fsub_rn(s, h[q]);
+        const float err = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, bv)), __fsub_rn(p, bv));
+        l[q] = __fadd_rn(l[q], __fadd_rn(err, e));
+        h[q] = s;
+    }
+    template <bool HAS_P>
+    __device__ __forceinline__ void add(const LsPending<float> &p) {
+        const float e0 = p.r - p.d0;
+        prod(0, e0, e0);
+        if (HAS_P) {
+            const float aa = p.d1 + p.d2, b = p.d3, m2e0 = -2.0f * e0;
+            prod(1, m2e0, aa);
+            prod(2, aa, aa);
+            prod(2, m2e0, b);
+            prod(3, 2.0f * aa, b);
+            prod(4, b, b);
+        }
+    }
+    __device__ __forceinline__ void out(double (&o)[5]) const {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) o[q] = (double)h[q] + (double)l[q];
+    }
+};
+
+template <typename T, bool HAS_P>
+__device__ __forceinline__ void ls_flush(LsPending<T> &q, LsAcc<T> &t) {
+    if (!q.have) return;
+    t.template add<HAS_P>(q);
     q.have = false;
 }
 
@@ -363,7 +424,7 @@ template <typename T, int LPR, bool HAS_P>
 __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4], const T *Xo,
                                               const T *Po, int64_t j, float r, int ld, int gl,
                                               bool act, unsigned mask, int &owner, LsPending<T> &q,
-                                              double (&t)[5]) {
+                                              LsAcc<T> &t) {
     T xm[4], pm[4];
     if (act) {
         ld4(Xo + j * ld + 4 * gl, xm);
@@ -395,7 +456,7 @@ __device__ __forceinline__ void lscoef_rating(const T (&xu)[4], const T (&pu)[4]
 template <typename T, int LPR, bool HAS_P>
 __device__ __forceinline__ void lscoef_range(const PassArgs &a, const T (&xu)[4], const T (&pu)[4], const T *Xo,
                                              const T *Po, int64_t e, int64_t e1, int gl, int lane, bool act,
-                                             unsigned mask, int &owner, LsPending<T> &q, double (&t)[5]) {
+                                             unsigned mask, int &owner, LsPending<T> &q, LsAcc<T> &t) {
     if constexpr (sizeof(T) == 4 && LPR == 32 && HAS_P) {
         for (; e + 2 <= e1; e += 2) {
             const int64_t j0 = a.idx[e], j1 = a.idx[e + 1];
@@ -481,12 +542,15 @@ __global__ void __launch_bounds__(256) k_lscoef(PassArgs a) {
         } else {
             zero4(xu); zero4(pu);
         }
-        double t[5] = {0, 0, 0, 0, 0};
+        LsAcc<T> acc;
+        acc.init();
         int owner = 0;
         LsPending<T> q;
         q.have = false;
-        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, beg, beg + n, gl, lane, act, mask, owner, q, t);
-        ls_flush<T, HAS_P>(q, t);
+        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, beg, beg + n, gl, lane, act, mask, owner, q, acc);
+        ls_flush<T, HAS_P>(q, acc);
+        double t[5];
+        acc.out(t);
         lscoef_finish<T, LPR, HAS_P>(a, row, n, gl, lane, mask, xu, pu, t);
     }
 }
@@ -512,12 +576,15 @@ __global__ void __launch_bounds__(256) k_lscoef_heavy(PassArgs a) {
         } else {
             zero4(xu); zero4(pu);
         }
-        double t[5] = {0, 0, 0, 0, 0};
+        LsAcc<T> acc;
+        acc.init();
         int owner = 0;
         LsPending<T> q;
         q.have = false;
-        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, e0, e1, gl, lane, act, mask, owner, q, t);
-        ls_flush<T, HAS_P>(q, t);
+        lscoef_range<T, LPR, HAS_P>(a, xu, pu, Xo, Po, e0, e1, gl, lane, act, mask, owner, q, acc);
+        ls_flush<T, HAS_P>(q, acc);
+        double t[5];
+        acc.out(t);
         if constexpr (HAS_P) tsum_n<LPR, 5>(t, mask, lane);
         else t[0] = gsum<LPR>(t[0], mask);
         if (gl == 0)

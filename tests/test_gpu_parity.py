@@ -192,6 +192,40 @@ def test_alsncg_trajectory_fp64(tiny):
             assert abs(info["gnorm"] - ref[k].gnorm) <= 1e-9 * g0, k
 
 
+def test_pinned_host_buffers_and_out_arrays(tiny):
+    """Inputs from pinned host tensors (ratings, x_0) and factors read into
+    given arrays (pinned host, numpy, device) give the same bits as the
+    numpy path; wrong out arrays are rejected."""
+    import torch
+    r, _, x0 = tiny
+    nu_f = r.n_u * r.n_f
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    with _model(r, precision="mixed") as m:
+        m.set_x(x0)
+        m.run(3, 0.0, check_every=3)
+        U, M = m.get_factors()
+    with _als()(r.n_u, r.n_m, pin(r.rows), pin(r.cols), pin(r.vals), r.n_f, r.lam, precision="mixed") as m:
+        m.set_factors(pin(x0[:nu_f].reshape(r.n_u, r.n_f)), pin(x0[nu_f:].reshape(r.n_m, r.n_f)))
+        m.run(3, 0.0, check_every=3)
+        Up = torch.empty((r.n_u, r.n_f), dtype=torch.float64, pin_memory=True)
+        Mp = torch.empty((r.n_m, r.n_f), dtype=torch.float64, pin_memory=True)
+        assert m.get_factors(out=(Up, Mp))[0] is Up
+        assert np.array_equal(Up.numpy(), U) and np.array_equal(Mp.numpy(), M)
+        Un, Mn = np.empty((r.n_u, r.n_f), np.float32), np.empty((r.n_m, r.n_f), np.float32)
+        m.get_factors("float32", out=(Un, Mn))
+        assert np.array_equal(Un, U.astype(np.float32)) and np.array_equal(Mn, M.astype(np.float32))
+        Ud = torch.empty((r.n_u, r.n_f), dtype=torch.float64, device="cuda")
+        Md = torch.empty((r.n_m, r.n_f), dtype=torch.float64, device="cuda")
+        m.get_factors(out=(Ud, Md))
+        assert np.array_equal(Ud.cpu().numpy(), U) and np.array_equal(Md.cpu().numpy(), M)
+        with pytest.raises(ValueError):
+            m.get_factors(out=(Un, Mn))                       # float32 arrays for float64
+        with pytest.raises(ValueError):
+            m.get_factors(out=(Up, Md))                       # host and device
+        with pytest.raises(ValueError):
+            m.get_factors(out=(Up[:, :2], Mp))                # wrong shape
+
+
 def test_state_roundtrip_resumes_identically(tiny):
     """Checkpoint / resume: get_state after 5 iterations, 5 more iterations;
     set_state from the checkpoint, 5 more: bit-identical."""
