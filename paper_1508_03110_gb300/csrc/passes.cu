@@ -343,14 +343,16 @@ struct LsPending {
 };
 
 // A lane's sums of the five rating terms of Q.  FP64 form: FP64 terms, FP64
-// sums.  Mixed form: the terms are formed in FP32 from the FP32 dot products
-// (one rounding each, below the dot products' own error), every product is
-// split exactly into two floats (x y = p + e, e = fma(x, y, -p)) and the sums
-// are kept as float pairs (hi, lo) by Knuth's two-sum, which carries the
-// rounding error of every addition (Knuth, TAOCP vol. 2, 4.2.2; Dekker 1971).
-// That keeps a lane's sum near FP64 accuracy while the FP64 pipe, 1/64 of
-// the FP32 rate here, is used once per row (to add hi and lo) instead of
-// about 17 times per 32 ratings.
+// sums.  Mixed form, without the FP64 pipe (1/64 of the FP32 rate here):
+// e0 = r - d0 and a = d1 + d2 are formed exactly as float pairs by Knuth's
+// two-sum, each product as its exact leading part (x y = p + e, e = fma(x, y,
+// -p)) plus the cross terms of the pairs' low parts, and the five sums are
+// kept as float pairs (hi, lo) by two-sum, which carries the rounding error of
+// every addition (Knuth, TAOCP vol. 2, 4.2.2; Dekker 1971).  Every term then
+// matches the one formed in FP64 from the same FP32 dot products to about
+// 2^-47 of itself and a lane's sum keeps FP64-like accuracy; the FP64 pipe
+// adds hi and lo once per row instead of taking about 17 instructions per 32
+// ratings.
 template <typename T>
 struct LsAcc {
     double t[5];
@@ -378,6 +380,14 @@ struct LsAcc {
     }
 };
 
+// s + e = a + b exactly (two-sum); the _rn intrinsics are never contracted
+// into an FMA, which would break the exact splits
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
 template <>
 struct LsAcc<float> {
     float h[5], l[5];
@@ -385,26 +395,29 @@ struct LsAcc<float> {
 #pragma unroll
         for (int q = 0; q < 5; ++q) h[q] = l[q] = 0.0f;
     }
-    // (h, l) += x y; the _rn intrinsics are never contracted into an FMA,
-    // which would break the exact splits
-    __device__ __forceinline__ void prod(int q, float x, float y) {
-        const float p = __fmul_rn(x, y), e = fmaf(x, y, -p);
-        const float s = __fadd_rn(h[q], p), bv = __fsub_rn(s, h[q]);
-        const float err = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, bv)), __fsub_rn(p, bv));
-        l[q] = __fadd_rn(l[q], __fadd_rn(err, e));
+    // (h, l) += (xh + xl)(yh + yl), dropping xl yl (2^-48 of the product)
+    __device__ __forceinline__ void prod(int q, float xh, float xl, float yh, float yl) {
+        const float p = __fmul_rn(xh, yh), e = fmaf(xh, yh, -p);
+        const float c = fmaf(xh, yl, __fmul_rn(xl, yh));
+        float s, err;
+        two_sum(h[q], p, s, err);
         h[q] = s;
+        l[q] = __fadd_rn(l[q], __fadd_rn(err, __fadd_rn(e, c)));
     }
     template <bool HAS_P>
     __device__ __forceinline__ void add(const LsPending<float> &p) {
-        const float e0 = p.r - p.d0;
-        prod(0, e0, e0);
+        float e0h, e0l;
+        two_sum(p.r, -p.d0, e0h, e0l);
+        prod(0, e0h, e0l, e0h, e0l);
         if (HAS_P) {
-            const float aa = p.d1 + p.d2, b = p.d3, m2e0 = -2.0f * e0;
-            prod(1, m2e0, aa);
-            prod(2, aa, aa);
-            prod(2, m2e0, b);
-            prod(3, 2.0f * aa, b);
-            prod(4, b, b);
+            float ah, al;
+            two_sum(p.d1, p.d2, ah, al);
+            const float b = p.d3;
+            prod(1, -2.0f * e0h, -2.0f * e0l, ah, al);
+            prod(2, ah, al, ah, al);
+            prod(2, -2.0f * e0h, -2.0f * e0l, b, 0.0f);
+            prod(3, 2.0f * ah, 2.0f * al, b, 0.0f);
+            prod(4, b, 0.0f, b, 0.0f);
         }
     }
     __device__ __forceinline__ void out(double (&o)[5]) const {
